@@ -1,0 +1,222 @@
+"""CPU FP64 oracle for the shared-Jacobian FNLH linear systems.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may use this package; the library never does.
+
+The arithmetic lives in ``fnlh_oracle.c`` (plain C, FP64, no FMA contraction,
+OpenMP over rows only); this module compiles it with gcc on first use and
+wraps it with ctypes.  Paper: arXiv 2404.01407 -- the implicit LHS of
+Eq. precon, its harmonic form Eq. precon_linear / Eq. lhs_lin, the block-Jacobi
+inversion of "Solution Update" and the linear residual of the Results
+section's stopping rule.  The readings taken where the paper is silent are
+listed at the top of ``fnlh_oracle.c``.
+
+Parity pins (tests/test_oracle_pins.py) tie every function here to something
+other than itself: the textbook Euler flux Jacobian and its eigenvalues, an
+eigendecomposition of |A|, complex-step derivatives of a frozen-dissipation
+first-order residual, closed forms on a uniform state, dense direct solves,
+the real 2x2-block form of Eq. matrix_z_real, and hand-solvable one- and
+two-node systems.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fnlh_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GAMMA = 1.4
+DELTA = 0.1
+EPS = 0.6
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP)."""
+    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(ctypes.CDLL(_LIB_PATH))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    lib.oracle_flux_jacobian.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_double, _f64p]
+    lib.oracle_flux_jacobian.restype = None
+    lib.oracle_abs_jacobian.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_double,
+                                        ctypes.c_double, _f64p]
+    lib.oracle_abs_jacobian.restype = None
+    lib.oracle_spectral_radius.argtypes = [_f64p, _f64p, ctypes.c_double]
+    lib.oracle_spectral_radius.restype = ctypes.c_double
+    lib.oracle_build_jacobian.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _f64p, _f64p, ctypes.c_double,
+        ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, _i32p, _i32p,
+        _f64p, _f64p, _f64p]
+    lib.oracle_build_jacobian.restype = ctypes.c_int
+    common = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p,
+              _f64p, _f64p, _f64p]
+    lib.oracle_jacobi.argtypes = common + [_f64p, ctypes.c_int]
+    lib.oracle_jacobi.restype = ctypes.c_int
+    lib.oracle_residual.argtypes = common + [_f64p, ctypes.c_void_p, _f64p]
+    lib.oracle_residual.restype = ctypes.c_int
+    lib.oracle_num_threads.argtypes = []
+    lib.oracle_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def use_library(path):
+    """Swap the loaded oracle for another build of ``fnlh_oracle.c`` (the
+    mutation tests load deliberately broken copies); returns the previous
+    library handle so that it can be restored with :func:`restore_library`."""
+    global _lib
+    prev = _load()
+    with _lock:
+        _lib = _bind(ctypes.CDLL(path))
+    return prev
+
+
+def restore_library(handle):
+    global _lib
+    with _lock:
+        _lib = handle
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def flux_jacobian(q, n, gamma: float = GAMMA) -> np.ndarray:
+    """A(Q, n) = d(F(Q).n)/dQ (complex-step)."""
+    q = _f64(q)
+    b = q.shape[0]
+    out = np.zeros(b * b)
+    _load().oracle_flux_jacobian(b, q, _f64(n), gamma, out)
+    return out.reshape(b, b)
+
+
+def abs_jacobian(q, n, gamma: float = GAMMA, delta: float = DELTA) -> np.ndarray:
+    """|A|(Q, n) with the entropy fix (Sylvester's formula)."""
+    q = _f64(q)
+    b = q.shape[0]
+    out = np.zeros(b * b)
+    _load().oracle_abs_jacobian(b, q, _f64(n), gamma, delta, out)
+    return out.reshape(b, b)
+
+
+def spectral_radius(q, n, gamma: float = GAMMA) -> float:
+    return float(_load().oracle_spectral_radius(_f64(q), _f64(n), gamma))
+
+
+class Jacobian:
+    """Oracle Jacobian: CSR pattern, off-diagonal and diagonal blocks, D."""
+
+    def __init__(self, row_ptr, col_idx, offd, diag, D, block):
+        self.row_ptr, self.col_idx, self.offd, self.diag, self.D = row_ptr, col_idx, offd, diag, D
+        self.block = block
+
+    @property
+    def n_nodes(self):
+        return int(self.D.shape[0])
+
+    @property
+    def nnz(self):
+        return int(self.col_idx.shape[0])
+
+
+def build_jacobian(n_nodes, edge_nodes, normals, q, cfl, gamma=GAMMA, delta=DELTA,
+                   pseudo_block=False, eps=EPS) -> Jacobian:
+    """First-order edge Jacobian J, diagonal blocks and pseudo-time diagonal D."""
+    q = _f64(q)
+    b = q.shape[1]
+    en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
+    E = en.shape[0]
+    row_ptr = np.zeros(n_nodes + 1, dtype=np.int32)
+    col_idx = np.zeros(max(2 * E, 1), dtype=np.int32)
+    offd = np.zeros(max(2 * E, 1) * b * b)
+    diag = np.zeros(n_nodes * b * b)
+    D = np.zeros(n_nodes)
+    rc = _load().oracle_build_jacobian(n_nodes, E, b, en.ravel(), _f64(normals).ravel(), q.ravel(),
+                                      gamma, delta, cfl, int(bool(pseudo_block)), eps, row_ptr,
+                                      col_idx, offd, diag, D)
+    if rc != 0:
+        raise ValueError(f"oracle_build_jacobian failed ({rc})")
+    return Jacobian(row_ptr, col_idx[: 2 * E].copy(), offd[: 2 * E * b * b].reshape(2 * E, b, b),
+                    diag.reshape(n_nodes, b, b), D, b)
+
+
+def _sys_args(jac: Jacobian, vol, omega):
+    b = jac.block
+    offd = _f64(jac.offd).ravel()
+    if offd.size == 0:
+        offd = np.zeros(1)
+    col = jac.col_idx if jac.col_idx.size else np.zeros(1, dtype=np.int32)
+    return (jac.n_nodes, b, int(np.asarray(omega).shape[0]), jac.row_ptr, col, offd,
+            _f64(jac.diag).ravel(), _f64(jac.D), _f64(vol), _f64(np.atleast_1d(omega)) if len(omega) else np.zeros(1))
+
+
+def jacobi(jac: Jacobian, vol, omega, B, sweeps: int, X0=None) -> np.ndarray:
+    """x after `sweeps` undamped block-Jacobi sweeps from X0 (zero if None)."""
+    B = _f64(B)
+    X = np.zeros_like(B) if X0 is None else _f64(X0).copy()
+    rc = _load().oracle_jacobi(*_sys_args(jac, vol, omega), B.ravel(), X.reshape(-1), int(sweeps))
+    if rc != 0:
+        raise FloatingPointError("singular diagonal block")
+    return X
+
+
+def residual(jac: Jacobian, vol, omega, B, X, want_r: bool = False):
+    """Returns (norms[K,2] = (||r_k||^2, ||B_k||^2), r or None)."""
+    B = _f64(B)
+    X = _f64(X)
+    K = 1 + len(omega)
+    norms = np.zeros(2 * K)
+    r = np.zeros_like(B) if want_r else None
+    rp = r.ctypes.data_as(ctypes.c_void_p) if want_r else None
+    _load().oracle_residual(*_sys_args(jac, vol, omega), B.ravel(), X.ravel(), rp, norms)
+    return norms.reshape(K, 2), r
+
+
+def rel_residuals(jac: Jacobian, vol, omega, B, X) -> np.ndarray:
+    """||B_k - A_k x_k|| / ||B_k|| per system k (mean first)."""
+    norms, _ = residual(jac, vol, omega, B, X)
+    return np.sqrt(norms[:, 0] / np.maximum(norms[:, 1], 1e-300))
+
+
+def solve_to_tol(jac: Jacobian, vol, omega, B, tol: float, chunk: int = 10, max_sweeps: int = 100000):
+    """Plain FP64 Jacobi until every system's relative residual <= tol."""
+    X = np.zeros_like(_f64(B))
+    done = 0
+    while done < max_sweeps:
+        X = jacobi(jac, vol, omega, B, chunk, X0=X)
+        done += chunk
+        if np.all(rel_residuals(jac, vol, omega, B, X) <= tol):
+            break
+    return X, done

@@ -1,0 +1,218 @@
+"""Seeded synthetic inputs for the shared-Jacobian FNLH linear systems.
+
+This module only *draws* inputs: a perturbed hexahedral node cloud with its
+edge graph, dual-face normals and control volumes, a near-uniform conservative
+flow state, and the right-hand sides of the mean-flow and harmonic systems.  It
+holds none of the method's arithmetic (no flux, Jacobian, pseudo-time term,
+block solve or residual); both the CUDA path and the CPU oracle consume what
+it returns, and neither imports the other.
+
+Recipe (the paper's cases are proprietary turbomachinery meshes, so these
+seeded stand-ins take their place; node counts and harmonic counts follow the
+compressor / turbine / LPC sizes of the Results section):
+
+* mesh (seed 1): nx*ny*nz hex lattice with unit spacing, node id
+  ``i + nx*(j + ny*k)``, every node moved by U(-0.1, 0.1) per axis (a +/-10%
+  perturbation); edges join lattice neighbours along +x, +y, +z (all x-edges
+  in node order, then y-edges, then z-edges); the dual-face normal of edge
+  (i, j) is ``x_j - x_i``; the control volume is the product over the three
+  axes of half the distance between the two axis neighbours (one-sided half
+  distance on the lattice boundary).
+* state (seed 2): gamma = 1.4, p = 1/gamma, rho = 1 + U(-0.02, 0.02),
+  Mach = 0.5 + U(-0.05, 0.05) along +x, v = w = 0; with 6 equations the sixth
+  conserved variable is rho * 0.01 (a constant SA working variable).
+* right-hand sides (seed 3): B = -R with R_mean ~ N(0, 1) (real) and every
+  harmonic R_l a standard complex normal (real and imaginary parts N(0, 1/2)).
+
+Layout of B and X: real ``[n][C][b]`` with ``C = 1 + 2N``: column 0 is the
+mean flow, columns ``2l-1`` and ``2l`` hold Re and Im of harmonic ``l``.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = 1.4
+NU_TILDE = 0.01
+
+
+@dataclass
+class Mesh:
+    """Edge-based node-centred mesh (host arrays)."""
+
+    dims: tuple
+    positions: np.ndarray  # [n][3] f64
+    edge_nodes: np.ndarray  # [E][2] int32, edge_nodes[e] = (i, j), i < j
+    normals: np.ndarray  # [E][3] f64, dual-face normal n_ij (from i to j)
+    vol: np.ndarray  # [n] f64
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.vol.shape[0])
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_nodes.shape[0])
+
+
+def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1) -> Mesh:
+    """Perturbed hex lattice treated as an unstructured edge mesh."""
+    n = nx * ny * nz
+    rng = np.random.default_rng(seed)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    base = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    pos = base + rng.uniform(-perturb, perturb, size=(n, 3))
+    ids = np.arange(n, dtype=np.int64).reshape(nz, ny, nx)
+
+    edges = []
+    if nx > 1:
+        edges.append(np.stack([ids[:, :, :-1].ravel(), ids[:, :, 1:].ravel()], axis=1))
+    if ny > 1:
+        edges.append(np.stack([ids[:, :-1, :].ravel(), ids[:, 1:, :].ravel()], axis=1))
+    if nz > 1:
+        edges.append(np.stack([ids[:-1, :, :].ravel(), ids[1:, :, :].ravel()], axis=1))
+    if edges:
+        en = np.concatenate(edges, axis=0)
+    else:
+        en = np.zeros((0, 2), dtype=np.int64)
+    normals = pos[en[:, 1]] - pos[en[:, 0]] if len(en) else np.zeros((0, 3))
+
+    # control volume: product over axes of half the neighbour span
+    p3 = pos.reshape(nz, ny, nx, 3)
+    vol = np.ones((nz, ny, nx))
+    for axis, size in ((2, nx), (1, ny), (0, nz)):
+        if size == 1:
+            continue  # no neighbours along this axis: unit extent
+        fwd = np.roll(p3, -1, axis=axis)
+        bwd = np.roll(p3, 1, axis=axis)
+        span = 0.5 * np.linalg.norm(fwd - bwd, axis=-1)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[axis] = 0
+        hi[axis] = size - 1
+        lo_nb = list(lo)
+        lo_nb[axis] = 1
+        hi_nb = list(hi)
+        hi_nb[axis] = size - 2
+        span[tuple(lo)] = 0.5 * np.linalg.norm(p3[tuple(lo_nb)] - p3[tuple(lo)], axis=-1)
+        span[tuple(hi)] = 0.5 * np.linalg.norm(p3[tuple(hi)] - p3[tuple(hi_nb)], axis=-1)
+        vol = vol * span
+    return Mesh(
+        dims=(nx, ny, nz),
+        positions=pos,
+        edge_nodes=np.ascontiguousarray(en, dtype=np.int32),
+        normals=np.ascontiguousarray(normals, dtype=np.float64),
+        vol=np.ascontiguousarray(vol.ravel(), dtype=np.float64),
+    )
+
+
+def custom_mesh(positions, edge_nodes, vol=None) -> Mesh:
+    """Mesh from explicit positions and edges (tiny hand-made cases)."""
+    pos = np.asarray(positions, dtype=np.float64).reshape(-1, 3)
+    en = np.asarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
+    normals = pos[en[:, 1]] - pos[en[:, 0]] if len(en) else np.zeros((0, 3))
+    if vol is None:
+        vol = np.ones(pos.shape[0])
+    return Mesh(dims=(pos.shape[0], 1, 1), positions=pos, edge_nodes=en,
+                normals=np.ascontiguousarray(normals), vol=np.asarray(vol, dtype=np.float64))
+
+
+def permute_mesh(mesh: Mesh, seed: int = 4) -> tuple[Mesh, np.ndarray]:
+    """Randomly renumber the nodes (locality stress variant). Returns (mesh, perm)
+    where new node ``p`` is old node ``perm[p]``."""
+    n = mesh.n_nodes
+    perm = np.random.default_rng(seed).permutation(n)
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    en = inv[mesh.edge_nodes.astype(np.int64)]
+    swap = en[:, 0] > en[:, 1]
+    normals = np.where(swap[:, None], -mesh.normals, mesh.normals)
+    en = np.sort(en, axis=1)
+    return Mesh(dims=mesh.dims, positions=mesh.positions[perm], edge_nodes=en.astype(np.int32),
+                normals=np.ascontiguousarray(normals), vol=mesh.vol[perm].copy()), perm
+
+
+def flow_state(n: int, block: int, seed: int = 2, uniform: bool = False) -> np.ndarray:
+    """Near-uniform conservative state Q[n][b] = (rho, rho u, rho v, rho w, rho E[, rho nu])."""
+    if block not in (5, 6):
+        raise ValueError("block must be 5 or 6")
+    rng = np.random.default_rng(seed)
+    if uniform:
+        rho = np.ones(n)
+        mach = np.full(n, 0.5)
+    else:
+        rho = 1.0 + rng.uniform(-0.02, 0.02, n)
+        mach = 0.5 + rng.uniform(-0.05, 0.05, n)
+    p = np.full(n, 1.0 / GAMMA)
+    a = np.sqrt(GAMMA * p / rho)
+    u = mach * a
+    q = np.zeros((n, block))
+    q[:, 0] = rho
+    q[:, 1] = rho * u
+    q[:, 4] = p / (GAMMA - 1.0) + 0.5 * rho * u * u
+    if block == 6:
+        q[:, 5] = rho * NU_TILDE
+    return q
+
+
+def rhs(n: int, block: int, n_harm: int, seed: int = 3) -> np.ndarray:
+    """B = -R in the [n][1+2N][b] layout."""
+    rng = np.random.default_rng(seed)
+    r0 = rng.standard_normal((n, block))
+    rh = rng.standard_normal((n, n_harm, 2, block)) * np.sqrt(0.5)
+    b = np.empty((n, 1 + 2 * n_harm, block))
+    b[:, 0, :] = -r0
+    b[:, 1:, :] = -rh.reshape(n, 2 * n_harm, block)
+    return b
+
+
+def omegas(n_harm: int, base: float = 1.0) -> np.ndarray:
+    """omega_l = l * base, l = 1..N."""
+    return base * np.arange(1, n_harm + 1, dtype=np.float64)
+
+
+@dataclass
+class Problem:
+    mesh: Mesh
+    q: np.ndarray
+    b: np.ndarray
+    omega: np.ndarray
+    block: int
+    cfl: float
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_harm(self) -> int:
+        return int(self.omega.shape[0])
+
+    @property
+    def n_cols(self) -> int:
+        return 1 + 2 * self.n_harm
+
+
+def problem(dims, block, n_harm, cfl, omega_base=1.0, seeds=(1, 2, 3), name="") -> Problem:
+    mesh = hex_mesh(*dims, seed=seeds[0])
+    q = flow_state(mesh.n_nodes, block, seed=seeds[1])
+    b = rhs(mesh.n_nodes, block, n_harm, seed=seeds[2])
+    return Problem(mesh=mesh, q=q, b=b, omega=omegas(n_harm, omega_base), block=block, cfl=cfl, name=name)
+
+
+# Workload table: the five configurations of the measurement plan.
+CONFIGS = {
+    "c1": dict(dims=(16, 8, 8), block=5, n_harm=1, cfl=10.0, omega_base=1.0, sweeps=20),
+    "c2": dict(dims=(128, 64, 48), block=6, n_harm=4, cfl=20.0, omega_base=1.0, sweeps=50),
+    "c3": dict(dims=(160, 128, 102), block=6, n_harm=8, cfl=20.0, omega_base=1.0, tol=1e-8),
+    "c4_row0": dict(dims=(80, 50, 50), block=6, n_harm=2, cfl=20.0, omega_base=1.0),
+    "c4_row1": dict(dims=(100, 75, 80), block=6, n_harm=8, cfl=20.0, omega_base=1.6),
+    "c4_row2": dict(dims=(125, 110, 80), block=6, n_harm=4, cfl=20.0, omega_base=2.3),
+    "c5": dict(dims=(256, 200, 156), block=6, n_harm=16, cfl=20.0, omega_base=1.0, tol=1e-8),
+}
+
+
+def config_problem(key: str, **overrides) -> Problem:
+    c = dict(CONFIGS[key])
+    c.update(overrides)
+    return problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c.get("omega_base", 1.0), name=key)
