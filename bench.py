@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the shared-Jacobian FNLH relaxation on GB300.
+
+Workload (the FP64 GPU baseline of the measurement plan): a 128x64x48
+perturbed hex passage (393,216 nodes, 1,162,240 edges), 6x6 blocks (Euler +
+one turbulence equation), mean flow + 4 harmonics at omega_n = n, CFL 20.
+One step = assemble J and D (+ Hessenberg prep) -> 50 FP64 block-Jacobi
+sweeps over all 5 systems -> FP64 residual norms.  value = node-system
+updates per second (n K sweeps / step time), whole job.
+
+Extra sections on the same line: the mixed-precision defect correction vs
+plain FP64 time to a 1e-8 relative residual (2.1M-node passage, 8
+harmonics), and the batched multi-row form (three blade rows of 200k/600k/
+1.1M nodes with 2/8/4 harmonics) against per-row launches.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnlh|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node·harmonic updates/s per Jacobi sweep; mixed vs FP64 time-to-1e-8 residual"
+UNIT = "updates/s"
+SWEEPS = 50
+WORKLOAD = "c2"
+
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
+# DRAM bytes per launch of the top kernel from the last ncu capture of the
+# kernel as it stands (None until captured for this version of the kernel)
+NCU_TRAFFIC = {}
+
+
+def hess_solve_flops(b: int, real: bool) -> int:
+    """Flops of one shifted Hessenberg solve (complex, or its real counterpart)."""
+    if real:
+        return 2 * b * (b - 1) + 4 * (b - 1) + b + 1
+    return 8 * b * (b - 1) + 19 * (b - 1) + 6 * b + 5
+
+
+def sweep_flops(n, nnz, b, n_harm):
+    C = 1 + 2 * n_harm
+    return 2.0 * nnz * b * b * C + n * (n_harm * hess_solve_flops(b, False) + hess_solve_flops(b, True))
+
+
+def sweep_bytes(n, nnz, b, n_harm, s_j, s_d, s_x, s_b):
+    """Algorithmic bytes of one sweep: each block once, X gathered once, X written once, B once."""
+    C = 1 + 2 * n_harm
+    return nnz * (b * b * s_j + 4) + n * (4 + b * b * s_d + 16) + n * b * C * (2 * s_x + s_b)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(p, budget_s=15.0, max_sweeps=30):
+    """The oracle as it stands on the host cores: one build, S sweeps, one residual."""
+    import oracle
+
+    m = p.mesh
+    t0 = time.perf_counter()
+    oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    X = oracle.jacobi(oj, m.vol, p.omega, p.b, 1)
+    t1 = time.perf_counter() - t0
+    S = int(max(1, min(max_sweeps, (budget_s - t_build) / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    X = oracle.jacobi(oj, m.vol, p.omega, p.b, S, X0=X)
+    oracle.residual(oj, m.vol, p.omega, p.b, X)
+    t = time.perf_counter() - t0
+    K = 1 + p.n_harm
+    return {"value": m.n_nodes * K * S / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{p.name} full mesh, {S} FP64 Jacobi sweeps + 1 residual after 1 warm sweep "
+                      f"(build {t_build:.1f} s excluded), {t:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    import oracle
+    from paper_2404_01407_gb300 import inputs
+
+    p = inputs.config_problem(WORKLOAD)
+    m = p.mesh
+    K = 1 + p.n_harm
+    oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+    sweeps_per_step = 2
+    X = np.zeros_like(p.b)
+    for _ in range(args.warmup):
+        X = oracle.jacobi(oj, m.vol, p.omega, p.b, sweeps_per_step, X0=X)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X = oracle.jacobi(oj, m.vol, p.omega, p.b, sweeps_per_step, X0=X)
+        oracle.residual(oj, m.vol, p.omega, p.b, X)
+    t = time.perf_counter() - t0
+    value = m.n_nodes * K * sweeps_per_step * args.steps / t
+    sample = (f"{WORKLOAD} full mesh; each step {sweeps_per_step} FP64 Jacobi sweeps + 1 residual "
+              f"(Jacobian built once, untimed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_config(p):
+    return {"workload": f"{p.name}: {p.mesh.dims[0]}x{p.mesh.dims[1]}x{p.mesh.dims[2]} perturbed hex passage, "
+                        f"{p.mesh.n_nodes} nodes, {p.mesh.n_edges} edges, b={p.block}, mean + {p.n_harm} harmonics, "
+                        f"CFL {p.cfl:g}, {SWEEPS} FP64 block-Jacobi sweeps per step (+ Jacobian build + residual)",
+            "nodes": p.mesh.n_nodes, "edges": p.mesh.n_edges, "block": p.block, "harmonics": p.n_harm,
+            "sweeps_per_step": SWEEPS, "l2": "inputs larger than L2 (J alone 0.67 GB FP64)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_fnlh(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2404_01407_gb300 import fnlh, inputs
+
+    fnlh.lib()
+    peaks, peaks_kind = load_peaks()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p = inputs.config_problem(WORKLOAD)
+    n, E, b, N = p.mesh.n_nodes, p.mesh.n_edges, p.block, p.n_harm
+    K, nnz = 1 + N, 2 * E
+    dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+    J = fnlh.DeviceJacobian(dm, b, fnlh.FNLH_PREP_F64, dev)
+    params = fnlh.make_params(p.cfl)
+    Q = torch.from_numpy(p.q).to(dev)
+    B = torch.from_numpy(p.b).to(dev)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(n, b, N, dev)
+    norms = torch.empty((K, 2), dtype=torch.float64, device=dev)
+
+    def step():
+        fnlh.fnlh_build_jacobian(dm, Q, params, J)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, SWEEPS, fnlh.FNLH_F64, ws)
+        fnlh.fnlh_residual(dm, J, p.omega, B, X, norms=norms, ws=ws)
+
+    # kernels launched per step: build, hessenberg, rotate_offd, 2 rotate_in, sweeps, rotate_out, residual, reduce
+    launches_per_step = 3 + 2 + SWEEPS + 1 + 2
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sweep_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    for a, z in sweep_ev:  # torch creates the CUDA event on its first record
+        a.record(stream)
+        z.record(stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        fnlh.fnlh_set_sweep_events(*sweep_ev[s])
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    fnlh.fnlh_set_sweep_events(None, None)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    sweep_ms = sum(a.elapsed_time(z) for a, z in sweep_ev) / (args.steps * SWEEPS)
+    rel = np.sqrt(norms[:, 0].cpu().numpy() / norms[:, 1].cpu().numpy())
+
+    updates = n * K * SWEEPS
+    value = world * updates / (ms * 1e-3)
+    flops = sweep_flops(n, nnz, b, N)
+    achieved = flops / (sweep_ms * 1e-3)
+    bytes_alg = sweep_bytes(n, nnz, b, N, 8, 8, 8, 8)
+    roofline = {"bound": "alu", "kernel": "k_sweep<6,double,double> (FP64 fused sweep)",
+                "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_FLOPS,
+                "traffic": NCU_TRAFFIC.get("k_sweep_f64_c2"),
+                "peak_note": "FP64 peak from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+                             "not in MEASURED_PEAKS.json",
+                "sweep_ms": sweep_ms, "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+                "hbm_gbs_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9,
+                "hbm_frac_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Qh = torch.from_numpy(p.q).pin_memory()
+    Bh = torch.from_numpy(p.b).pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
+    nh = torch.empty((K, 2), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    for it in range(e2e_steps + 1):
+        if it == 1:
+            barrier(world)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+        Q.copy_(Qh, non_blocking=True)
+        B.copy_(Bh, non_blocking=True)
+        step()
+        Xh.copy_(X, non_blocking=True)
+        nh.copy_(norms, non_blocking=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(a0.elapsed_time(a1) / e2e_steps, world)
+    e2e = {"value": world * updates / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": Qh.numel() * 8 + Bh.numel() * 8,
+           "d2h_bytes_per_step": Xh.numel() * 8 + nh.numel() * 8, "ms_per_step": e2e_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hex passage; see DESIGN.md)",
+            "config": workload_config(p), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": ck,
+            "final_rel_residual": [float(x) for x in rel], "peaks_source": peaks_kind}
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        del J, ws
+        torch.cuda.empty_cache()
+        line["mixed_vs_fp64"] = mixed_section(torch, fnlh, inputs, dev)
+        torch.cuda.empty_cache()
+        line["batched"] = batched_section(torch, fnlh, inputs, dev, args)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
+    """Plain FP64 Jacobi vs defect correction (FP32 / BF16 blocks) to a 1e-8 FP64 residual."""
+    p = inputs.config_problem("c3")
+    n, b, N = p.mesh.n_nodes, p.block, p.n_harm
+    dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+    flags = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
+    J = fnlh.DeviceJacobian(dm, b, flags, dev)
+    fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+    B = torch.from_numpy(p.b).to(dev)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(n, b, N, dev)
+    out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, b=6, mean + {N} harmonics, CFL 20, tol {tol:g}"}
+    cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 12)]
+    for name, prec, inner in cases:
+        X.zero_()
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False)  # warm
+        X.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=ws,
+                                                  raise_on_error=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out[name] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
+                     "inner_sweeps": inner, "max_rel_residual": float(np.max(rel))}
+    if out["f64"]["status"] == "success":
+        for name in ("f32", "bf16"):
+            out[name]["speedup_vs_f64"] = out["f64"]["seconds"] / out[name]["seconds"]
+    return out
+
+
+def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16"):
+    """Three blade rows: one persistent launch per sweep (graph-captured) vs per-row launches."""
+    prec = fnlh.PRECISIONS[prec_name]
+    rows = []
+    for key in ("c4_row0", "c4_row1", "c4_row2"):
+        c = inputs.CONFIGS[key]
+        p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=key)
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+        J = fnlh.DeviceJacobian(dm, p.block, fnlh.PREP_FOR[prec], dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+        B = torch.from_numpy(p.b).to(dev)
+        rows.append((p, dm, J, B, torch.zeros_like(B), fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev)))
+    updates = sum(p.mesh.n_nodes * (1 + p.n_harm) for p, *_ in rows) * sweeps
+
+    def per_row():
+        for p, dm, J, B, X, ws in rows:
+            fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec, ws)
+
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
+    bws = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device=dev)
+
+    def batched(tn=None):
+        fnlh.fnlh_relax_batched(batch, sweeps, prec, tuning=tn, ws=bws)
+
+    def timeit(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    from paper_2404_01407_gb300 import autotune
+
+    best, table = autotune.tune_batched(lambda tn: timeit(lambda: batched(tn), reps=2))
+    t_rows = timeit(per_row)
+    t_batch = timeit(lambda: batched(best))
+    # CUDA graph of the whole batched call
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        batched(best)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            batched(best)
+    torch.cuda.current_stream().wait_stream(s)
+    t_graph = timeit(g.replay)
+    return {"workload": "c4: rows 80x50x50 (N=2), 100x75x80 (N=8), 125x110x80 (N=4), b=6, "
+                        f"{sweeps} {prec_name} sweeps", "per_row_ms": t_rows, "batched_ms": t_batch,
+            "batched_graph_ms": t_graph, "tuning": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm,
+                                                    "tile_pairs": best.nodes_per_tile},
+            "updates_per_s_graph": updates / (t_graph * 1e-3), "speedup_vs_per_row": t_rows / t_graph,
+            "tuning_table": table}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fnlh", choices=["fnlh", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fnlh(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * fnlh.h -- C ABI of the GB300 (sm_103a) shared-Jacobian FNLH linear solver.
+ *
+ * Paper: X. Wang, L. di Mare et al., "Convergence Acceleration of
+ * Favre-Averaged Non-Linear Harmonic Method", arXiv 2404.01407.
+ *
+ * The library relaxes, all at once, the sparse linear systems formed in one
+ * implicit RK stage by the mean flow and by every time-linearised harmonic
+ * (Eq. lhs_mean and Eq. lhs_lin, with the implicit left-hand side of
+ * Eq. precon / Eq. precon_linear):
+ *
+ *     A_k x_k = B_k,   A_k = J + D I + i omega_k V I,   k = 0..N
+ *
+ * J = dR/dQ is the first-order approximate residual Jacobian assembled from
+ * immediate neighbours ("Generalized RK Scheme for The Mean Flow"), D the
+ * scalar pseudo-time diagonal V_i/dt_i, V the control volume, omega_0 = 0 the
+ * mean flow.  One J and one D serve the mean flow and all harmonics, so no
+ * allocation here grows with N ("Solution Update": the LHS memory of all
+ * harmonics is shared).  The Gamma*alpha_k factor of Eq. lhs_mean is the
+ * caller's: scale B by Gamma*alpha_k to obtain the paper's update.
+ *
+ * Conventions
+ * -----------
+ *  - Every array argument is DEVICE memory owned by the caller unless the
+ *    comment says "host".  The library allocates no device memory: scratch
+ *    space is the caller's `workspace` (size from fnlh_workspace_bytes) and
+ *    derived Jacobian data is the caller's `prep` blob (size from
+ *    fnlh_prep_bytes).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it, except the ones documented as synchronising.
+ *  - Vectors X, B, r use the real layout [n][C][b], C = 1 + 2N: column 0 is
+ *    the mean flow, columns 2l-1 and 2l are Re and Im of harmonic l, whose
+ *    angular frequency is omega[l-1] (the +i omega sign of Eq. phi_fft).
+ *  - Blocks are row-major b x b, b = 5 (Euler) or 6 (Euler + one turbulence
+ *    equation).  Off-diagonal blocks are stored in CSR order [nnz][b][b];
+ *    within a row the neighbours are sorted ascending.
+ *  - Return value: FNLH_OK (0) or a negative FNLH_ERR_* code; arguments are
+ *    validated on the host before anything is launched, and nothing is
+ *    launched when validation fails.
+ */
+#ifndef FNLH_H
+#define FNLH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *fnlh_stream_t; /* a cudaStream_t */
+
+enum fnlh_status {
+    FNLH_OK = 0,
+    FNLH_ERR_ARG = -1,           /* invalid argument (null pointer, size, range) */
+    FNLH_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+    FNLH_ERR_NONFINITE = -3,     /* a residual norm is NaN or Inf */
+    FNLH_ERR_DIVERGED = -4,      /* residual grew by more than 1e3 over its start */
+    FNLH_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+    FNLH_ERR_UNSUPPORTED = -6,   /* block size not 5 or 6, too many harmonics */
+    FNLH_ERR_WORKSPACE = -7,     /* workspace or prep blob too small / missing */
+    FNLH_ERR_NOT_CONVERGED = -8, /* iteration limit reached above tolerance */
+    FNLH_ERR_BAD_MESH = -9       /* self loop, duplicate edge, node out of range */
+};
+
+/* Precision of a relaxation (storage of the off-diagonal blocks / iterate). */
+enum fnlh_precision {
+    FNLH_F64 = 0,  /* FP64 blocks, FP64 iterate and arithmetic */
+    FNLH_F32 = 1,  /* FP32 blocks, FP32 iterate and arithmetic */
+    FNLH_BF16 = 2  /* BF16 blocks, FP32 iterate and arithmetic */
+};
+
+/* Which derived off-diagonal copies fnlh_prepare writes (bit mask). */
+enum fnlh_prep_flags { FNLH_PREP_F64 = 1, FNLH_PREP_F32 = 2, FNLH_PREP_BF16 = 4 };
+
+#define FNLH_MAX_HARMONICS 64
+
+/* Edge-based node-centred mesh (paper, "Brief Description of Hydra": an
+ * edge data structure with dual-face normals).  Device arrays. */
+typedef struct fnlh_mesh {
+    int32_t n_nodes;
+    int32_t n_edges;
+    const int32_t *edge_nodes; /* [E][2] node pair (i, j) of each edge */
+    const double *normals;     /* [E][3] dual-face normal n_ij, pointing from i to j */
+    const double *vol;         /* [n] control volume V_i (spectral term i omega V) */
+    const int32_t *row_ptr;    /* [n+1] CSR of the symmetric neighbour graph */
+    const int32_t *col_idx;    /* [2E] neighbour of each CSR entry, ascending per row */
+    const int32_t *csr_edge;   /* [2E] edge of each CSR entry */
+} fnlh_mesh;
+
+/* Jacobian construction parameters. */
+typedef struct fnlh_params {
+    double gamma;         /* ratio of specific heats (1.4) */
+    double cfl;           /* pseudo-time CFL number sigma_CFL */
+    double entropy_delta; /* entropy fix: f(l) = max(|l|, delta (|u_n| + a|n|)); 0.1 */
+    int32_t pseudo_time;  /* 0: scalar D_i = V_i/dt_i; 1: block P/(eps sigma_CFL) of Eq. precon */
+    double eps;           /* relaxation factor eps of Eq. precon (0.6) */
+} fnlh_params;
+
+/* The shared operator.  offd/diag/D are written by fnlh_build_jacobian or
+ * supplied by the caller; prep is the caller-allocated derived blob
+ * (fnlh_prep_bytes) that fnlh_prepare fills with per-node Hessenberg factors
+ * and the off-diagonal copies named by prep_flags. */
+typedef struct fnlh_jacobian {
+    int32_t n_nodes;
+    int32_t nnz;       /* = 2 E */
+    int32_t block;     /* b: 5 or 6 */
+    double *offd;      /* [nnz][b][b] J_ij */
+    double *diag;      /* [n][b][b]   J_ii */
+    double *D;         /* [n]         pseudo-time diagonal */
+    void *prep;        /* derived data, fnlh_prep_bytes(n, nnz, b, prep_flags) bytes */
+    size_t prep_bytes;
+    int32_t prep_flags; /* FNLH_PREP_* mask */
+    int32_t prep_ready; /* set to 1 by fnlh_prepare, 0 by fnlh_build_jacobian */
+} fnlh_jacobian;
+
+/* One blade row of a batched relaxation (fnlh_relax_batched). */
+typedef struct fnlh_row {
+    const fnlh_mesh *mesh;
+    const fnlh_jacobian *J;
+    int32_t n_harm;
+    const double *omega; /* host [n_harm] */
+    const double *B;     /* [n][C][b] right-hand sides */
+    double *X;           /* [n][C][b] in: x0, out: x */
+} fnlh_row;
+
+/* Launch shape of the sweep kernels (0 = library default). */
+typedef struct fnlh_tuning {
+    int32_t threads;      /* threads per CTA */
+    int32_t ctas_per_sm;  /* persistent grid = SMs x this */
+    int32_t nodes_per_tile; /* nodes per work tile of the batched kernel */
+    int32_t reserved;
+} fnlh_tuning;
+
+/* Human-readable text of a status code (static storage). */
+const char *fnlh_strerror(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fnlh_version(void);
+
+/* HOST helper: CSR of the neighbour graph from an edge list.
+ * edge_nodes (host [E][2]); outputs (host) row_ptr [n+1], col_idx [2E],
+ * csr_edge [2E], neighbours ascending within each row.  Rejects self loops,
+ * duplicate edges and out-of-range nodes with FNLH_ERR_BAD_MESH. */
+int fnlh_mesh_build_csr(int32_t n_nodes, int32_t n_edges, const int32_t *edge_nodes,
+                        int32_t *row_ptr, int32_t *col_idx, int32_t *csr_edge);
+
+/* Bytes of the derived blob for fnlh_prepare. */
+size_t fnlh_prep_bytes(int32_t n_nodes, int32_t nnz, int32_t block, int32_t prep_flags);
+
+/* Bytes of scratch space any call below needs for this problem size. */
+size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm);
+
+/* Assemble J (off-diagonal and diagonal blocks) and D from the conservative
+ * state Q [n][b] (rho, rho u, rho v, rho w, rho E[, rho nu]) -- the
+ * first-order, immediate-neighbour residual Jacobian of Eq. precon:
+ *   J_ij = 1/2 (A(Q_j, n_ij) - |A|(Qbar_ij, n_ij))
+ *   J_ii = 1/2 sum_j |A|(Qbar_ij, n_ij) + 1/2 |A|(Q_i, n_b),  n_b = -sum_j n_ij
+ *   D_i  = (sum_j lambda(Qbar_ij, n_ij) + lambda(Q_i, n_b)) / CFL
+ * A = d(F.n)/dQ of the Euler flux (six equations: frozen turbulence row
+ * advected at u_n, its J_ii entry doubled), |A| its matrix absolute value with
+ * the entropy fix, lambda = |u_n| + a|n|, Qbar the arithmetic mean.  With
+ * params->pseudo_time = 1, D = 0 and J_ii is scaled by 1 + 1/(eps CFL).
+ * Then, if J->prep is set, runs fnlh_prepare.  Asynchronous. */
+int fnlh_build_jacobian(const fnlh_mesh *mesh, const double *Q, const fnlh_params *params,
+                        fnlh_jacobian *J, fnlh_stream_t stream);
+
+/* Derived data for the sweeps: per node an orthogonal Q_i with
+ * Q_i^T (J_ii + D_i I) Q_i upper Hessenberg, and the off-diagonal blocks
+ * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags.
+ * Depends only on J and D, so it is independent of the number of harmonics.
+ * Call after changing offd/diag/D yourself.  Asynchronous. */
+int fnlh_prepare(const fnlh_mesh *mesh, fnlh_jacobian *J, fnlh_stream_t stream);
+
+/* `sweeps` undamped block-Jacobi sweeps ("Solution Update": block-diagonal
+ * inversion point by point) on every system at once:
+ *   x_i <- (J_ii + (D_i + i omega_k V_i) I)^-1 (B_i - sum_j J_ij x_j)
+ * omega: HOST [n_harm].  B, X: FP64 [n][C][b]; X holds x0 on entry, the
+ * result on return.  precision selects the block copy and arithmetic of the
+ * sweeps (FNLH_F64 needs FNLH_PREP_F64, etc.).  Asynchronous. */
+int fnlh_relax(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
+               const double *B, double *X, int32_t sweeps, int32_t precision, void *workspace,
+               size_t workspace_bytes, fnlh_stream_t stream);
+
+/* FP64 linear residual r_k = B_k - A_k x_k (the quantity of the paper's
+ * linear-solve stopping rule, Results / Table fnlh_para) and, per system k,
+ * norms[2k] = ||r_k||_2^2, norms[2k+1] = ||B_k||_2^2 (complex 2-norm over all
+ * n b entries).  r (nullable) [n][C][b]; norms [2K] device.  The sums are
+ * reduced in a fixed order, so repeated calls give identical bits.
+ * Asynchronous. */
+int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
+                  const double *omega, const double *B, const double *X, double *r,
+                  double *norms, void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
+
+/* Solve every system to ||r_k|| <= tol ||B_k||.  precision FNLH_F64: plain FP64
+ * Jacobi with an FP64 residual check every `inner_sweeps` sweeps.
+ * FNLH_F32 / FNLH_BF16: defect correction -- FP64 residual r = B - A x,
+ * `inner_sweeps` sweeps on A e = r with the low-precision blocks and FP32
+ * arithmetic from e = 0, then x += e in FP64; repeated.  X: in x0, out x.
+ * SYNCHRONISING (reads the norms after every check).  Outputs (host, each
+ * nullable): *checks_done residual evaluations, *sweeps_done total sweeps,
+ * rel_res [K] final ||r_k||/||B_k||.  Returns FNLH_ERR_NOT_CONVERGED after
+ * max_checks checks above tol, FNLH_ERR_NONFINITE / FNLH_ERR_DIVERGED on a
+ * non-finite or growing (x1e3) residual. */
+int fnlh_solve(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
+               const double *B, double *X, int32_t precision, double tol, int32_t inner_sweeps,
+               int32_t max_checks, void *workspace, size_t workspace_bytes, int32_t *checks_done,
+               int32_t *sweeps_done, double *rel_res, fnlh_stream_t stream);
+
+/* Batched form: `sweeps` sweeps of fnlh_relax on several blade rows of
+ * different sizes and harmonic counts (the multi-row FNLH setting of the
+ * paper's Results) with one persistent kernel launch per sweep over a tile
+ * list spanning every row.  tuning may be NULL (defaults).  workspace: at
+ * least the sum of fnlh_workspace_bytes of the rows plus
+ * fnlh_batched_extra_bytes(n_rows).  Asynchronous, graph-capturable. */
+int fnlh_relax_batched(const fnlh_row *rows, int32_t n_rows, int32_t sweeps, int32_t precision,
+                       const fnlh_tuning *tuning, void *workspace, size_t workspace_bytes,
+                       fnlh_stream_t stream);
+
+size_t fnlh_batched_extra_bytes(int32_t n_rows);
+
+/* Timing hook (not part of the paper): when both are non-NULL, every later
+ * relaxation on this host thread records `begin` on its stream right before
+ * its first sweep launch and `end` right after its last one, so that the
+ * caller can time the sweep launches alone.  Events are cudaEvent_t created
+ * by the caller; pass NULL, NULL to switch the hook off. */
+int fnlh_set_sweep_events(void *begin, void *end);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNLH_H */

@@ -1,0 +1,218 @@
+// Internal helpers of the FNLH CUDA library (sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fnlh.h"
+
+namespace fnlh {
+
+constexpr int kMaxSys = FNLH_MAX_HARMONICS + 1;  // mean + harmonics
+constexpr int kResidualGrid = 1216;               // fixed grid of the residual kernels (deterministic sums)
+constexpr int kResidualThreads = 256;
+
+// Per-launch system description passed by value (omega baked into the launch).
+struct Systems {
+  int32_t K;             // systems = 1 + N
+  int32_t C;             // real columns = 1 + 2N
+  double omega[kMaxSys]; // omega[0] = 0 (mean), omega[l] harmonic l
+};
+
+// ------------------------------------------------------------------ loads
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+template <typename T> __device__ __forceinline__ T cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return (float)x; }
+
+template <typename TACC, typename T> __device__ __forceinline__ TACC ld(const T* p);
+template <> __device__ __forceinline__ double ld<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <> __device__ __forceinline__ float ld<float, double>(const double* p) { return (float)__ldg(p); }
+
+// ----------------------------------------------- shifted Hessenberg solve
+//
+// Solve (H + i s I) y = b for an upper Hessenberg H (row-major BS x BS,
+// entries below the subdiagonal are not read) and a real shift s, by
+// Gaussian elimination with partial pivoting between the two candidate rows
+// of each step (the only rows with a nonzero entry in the pivot column).
+// (yr, yi) holds b on entry and y on return.  Cost O(BS^2) complex
+// operations instead of the O(BS^3) of a general block LU.
+template <int BS, typename T, typename TH>
+__device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr)[BS], T (&yi)[BS]) {
+  // upper-triangular factor rows (complex); row k holds columns k..BS-1
+  T ur[BS][BS], ui[BS][BS];
+  T rr[BS], ri[BS];  // reciprocal of each pivot
+  // current candidate row for position k (row 0 initially)
+  T cr[BS], ci[BS], cbr, cbi;
+#pragma unroll
+  for (int c = 0; c < BS; ++c) {
+    cr[c] = ld<T>(H + c);
+    ci[c] = (c == 0) ? s : T(0);
+  }
+  cbr = yr[0];
+  cbi = yi[0];
+#pragma unroll
+  for (int k = 0; k < BS - 1; ++k) {
+    // next original row k+1: columns k..BS-1
+    T nr[BS], ni[BS];
+#pragma unroll
+    for (int c = k; c < BS; ++c) {
+      nr[c] = ld<T>(H + (k + 1) * BS + c);
+      ni[c] = (c == k + 1) ? s : T(0);
+    }
+    T nbr = yr[k + 1], nbi = yi[k + 1];
+    // pivot choice (1-norm magnitude)
+    const bool sw = (fabs(nr[k]) + fabs(ni[k])) > (fabs(cr[k]) + fabs(ci[k]));
+#pragma unroll
+    for (int c = k; c < BS; ++c) {
+      T tr = sw ? nr[c] : cr[c], ti = sw ? ni[c] : ci[c];
+      nr[c] = sw ? cr[c] : nr[c];
+      ni[c] = sw ? ci[c] : ni[c];
+      cr[c] = tr;
+      ci[c] = ti;
+    }
+    {
+      T tr = sw ? nbr : cbr, ti = sw ? nbi : cbi;
+      nbr = sw ? cbr : nbr;
+      nbi = sw ? cbi : nbi;
+      cbr = tr;
+      cbi = ti;
+    }
+    // pivot reciprocal
+    const T m2 = cr[k] * cr[k] + ci[k] * ci[k];
+    const T inv = T(1) / m2;
+    rr[k] = cr[k] * inv;
+    ri[k] = -ci[k] * inv;
+    // store pivot row
+#pragma unroll
+    for (int c = k; c < BS; ++c) {
+      ur[k][c] = cr[c];
+      ui[k][c] = ci[c];
+    }
+    yr[k] = cbr;
+    yi[k] = cbi;
+    // multiplier l = n_k / p
+    const T lr = nr[k] * rr[k] - ni[k] * ri[k];
+    const T li = nr[k] * ri[k] + ni[k] * rr[k];
+    // eliminate: new candidate = n - l * c  (columns k+1..)
+#pragma unroll
+    for (int c = k + 1; c < BS; ++c) {
+      const T ar = nr[c] - (lr * cr[c] - li * ci[c]);
+      const T ai = ni[c] - (lr * ci[c] + li * cr[c]);
+      cr[c] = ar;
+      ci[c] = ai;
+    }
+    const T br = nbr - (lr * cbr - li * cbi);
+    const T bi = nbi - (lr * cbi + li * cbr);
+    cbr = br;
+    cbi = bi;
+  }
+  {
+    const int k = BS - 1;
+    const T m2 = cr[k] * cr[k] + ci[k] * ci[k];
+    const T inv = T(1) / m2;
+    rr[k] = cr[k] * inv;
+    ri[k] = -ci[k] * inv;
+    yr[k] = cbr;
+    yi[k] = cbi;
+  }
+  // back substitution
+#pragma unroll
+  for (int k = BS - 1; k >= 0; --k) {
+    T ar = yr[k], ai = yi[k];
+#pragma unroll
+    for (int c = k + 1; c < BS; ++c) {
+      ar -= ur[k][c] * yr[c] - ui[k][c] * yi[c];
+      ai -= ur[k][c] * yi[c] + ui[k][c] * yr[c];
+    }
+    yr[k] = ar * rr[k] - ai * ri[k];
+    yi[k] = ar * ri[k] + ai * rr[k];
+  }
+}
+
+// ---------------------------------------------------------- workspace map
+//
+// [0, 256)                      status words (int32)
+// [256, +partials)              residual partial sums  kResidualGrid x 2K doubles
+// norms                         final 2K doubles of the last residual
+// vec0, vec1, vec2              three [n][C][b] vectors in the precision's type
+struct WsLayout {
+  size_t status, partials, norms, vec[3], total, vec_bytes;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t precision) {
+  WsLayout w;
+  const size_t K = 1 + (size_t)n_harm, C = 1 + 2 * (size_t)n_harm;
+  const size_t elem = (precision == FNLH_F64) ? 8 : 4;
+  w.status = 0;
+  w.partials = 256;
+  w.norms = w.partials + (size_t)kResidualGrid * 2 * K * sizeof(double);
+  size_t off = align256(w.norms + 2 * K * sizeof(double));
+  w.vec_bytes = (size_t)n * C * block * elem;
+  for (int v = 0; v < 3; ++v) {
+    w.vec[v] = off;
+    off = align256(off + w.vec_bytes);
+  }
+  w.total = off;
+  return w;
+}
+
+// ----------------------------------------------------------- prep blob map
+//
+// rot   [n][b][b] f64   Q_i
+// hess  [n][b][b] f64   Q_i^T (J_ii + D_i I) Q_i  (upper Hessenberg, zeros below)
+// hessf [n][b][b] f32   (when an F32/BF16 copy is requested)
+// offd64 / offd32 / offd16 [nnz][b][b] rotated off-diagonal copies
+struct PrepLayout {
+  size_t rot, hess, hessf, offd64, offd32, offd16, total;
+};
+
+inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) {
+  PrepLayout p;
+  const size_t bb = (size_t)b * b;
+  size_t off = 0;
+  p.rot = off;
+  off = align256(off + (size_t)n * bb * 8);
+  p.hess = off;
+  off = align256(off + (size_t)n * bb * 8);
+  p.hessf = p.offd64 = p.offd32 = p.offd16 = (size_t)-1;
+  if (flags & (FNLH_PREP_F32 | FNLH_PREP_BF16)) {
+    p.hessf = off;
+    off = align256(off + (size_t)n * bb * 4);
+  }
+  if (flags & FNLH_PREP_F64) {
+    p.offd64 = off;
+    off = align256(off + (size_t)nnz * bb * 8);
+  }
+  if (flags & FNLH_PREP_F32) {
+    p.offd32 = off;
+    off = align256(off + (size_t)nnz * bb * 4);
+  }
+  if (flags & FNLH_PREP_BF16) {
+    p.offd16 = off;
+    off = align256(off + (size_t)nnz * bb * 2);
+  }
+  p.total = off;
+  return p;
+}
+
+template <typename T> inline T* at(void* base, size_t off) { return reinterpret_cast<T*>((char*)base + off); }
+
+}  // namespace fnlh
+
+#define FNLH_CUDA_TRY(expr)                       \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return FNLH_ERR_CUDA;  \
+  } while (0)
+
+#define FNLH_LAUNCH_CHECK() FNLH_CUDA_TRY(cudaGetLastError())

@@ -1,0 +1,367 @@
+// Jacobian assembly and sweep preparation (FP64).
+//
+// Paper: arXiv 2404.01407, Eq. precon (implicit K = P/(eps sigma) + J with
+// J = dR/dQ "assembled using the information of the immediate neighbours with
+// first-order spatial accuracy") and "Solution Update" (J assembled once per
+// nonlinear iteration and shared by the mean flow and every harmonic).
+//
+// Both kernels here run once per nonlinear iteration, off the sweep loop.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace fnlh {
+
+// Closed-form Euler flux Jacobian d(F.n)/dQ for conservative Q and an
+// unnormalised face normal n; with six equations the sixth (turbulence)
+// variable is advected at u_n and does not feed back (frozen turbulence).
+template <int BS>
+__device__ __forceinline__ void flux_jacobian(const double (&q)[BS], const double n[3], double gamma,
+                                              double (&A)[BS][BS]) {
+  const double rho = q[0], ir = 1.0 / rho;
+  const double vel[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const double g1 = gamma - 1.0;
+  const double ke = 0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+  const double p = g1 * (q[4] - rho * ke);
+  const double H = (q[4] + p) * ir;
+  const double phi = g1 * ke;
+  const double un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) A[r][c] = 0.0;
+  A[0][1] = n[0];
+  A[0][2] = n[1];
+  A[0][3] = n[2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    A[1 + r][0] = n[r] * phi - vel[r] * un;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[1 + r][1 + c] = vel[r] * n[c] - g1 * vel[c] * n[r];
+    A[1 + r][1 + r] += un;
+    A[1 + r][4] = g1 * n[r];
+  }
+  A[4][0] = un * (phi - H);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) A[4][1 + c] = H * n[c] - g1 * vel[c] * un;
+  A[4][4] = gamma * un;
+  if (BS == 6) {
+    const double nu = q[BS - 1] * ir;
+    A[BS - 1][0] = -nu * un;
+    A[BS - 1][1] = nu * n[0];
+    A[BS - 1][2] = nu * n[1];
+    A[BS - 1][3] = nu * n[2];
+    A[BS - 1][BS - 1] = un;
+  }
+}
+
+__device__ __forceinline__ void sound_and_un(const double* q, const double n[3], double gamma, double& a,
+                                             double& un, double& nn) {
+  const double ir = 1.0 / q[0];
+  const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+  const double p = (gamma - 1.0) * (q[4] - 0.5 * q[0] * (u * u + v * v + w * w));
+  a = sqrt(gamma * p * ir);
+  un = u * n[0] + v * n[1] + w * n[2];
+  nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+}
+
+// |A|(Q, n) with the entropy fix f(l) = max(|l|, delta (|u_n| + a|n|)),
+// written through N = A - u_n I (rank two for the Euler block):
+//   |A| = f0 I + N^2 ((f+ + f-)/2 - f0) / c^2 + N (f+ - f-) / (2c),  c = a|n|,
+// which is the spectral form sum_k f(l_k) P_k with the projectors onto the
+// eigenspaces of u_n and u_n +- c.  Turbulence row: the scalar f(u_n).
+template <int BS>
+__device__ __forceinline__ void abs_flux_jacobian(const double (&q)[BS], const double n[3], double gamma,
+                                                  double delta, double (&M)[BS][BS]) {
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) M[r][c] = 0.0;
+  double a, un, nn;
+  sound_and_un(q, n, gamma, a, un, nn);
+  if (nn == 0.0) return;
+  double A[BS][BS];
+  flux_jacobian<BS>(q, n, gamma, A);
+  const double c = a * nn;
+  const double fix = delta * (fabs(un) + c);
+  const double f0 = fmax(fabs(un), fix), fp = fmax(fabs(un + c), fix), fm = fmax(fabs(un - c), fix);
+  const double s2 = (0.5 * (fp + fm) - f0) / (c * c);
+  const double s1 = (fp - fm) / (2.0 * c);
+  double N[5][5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) N[r][k] = A[r][k] - (r == k ? un : 0.0);
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double n2 = 0.0;
+#pragma unroll
+      for (int t = 0; t < 5; ++t) n2 += N[r][t] * N[t][k];
+      M[r][k] = s2 * n2 + s1 * N[r][k] + (r == k ? f0 : 0.0);
+    }
+  if (BS == 6) M[5][5] = f0;
+}
+
+__device__ __forceinline__ double spectral_radius(const double* q, const double n[3], double gamma) {
+  double a, un, nn;
+  sound_and_un(q, n, gamma, a, un, nn);
+  return fabs(un) + a * nn;
+}
+
+struct BuildArgs {
+  int32_t n;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const int32_t* csr_edge;
+  const int32_t* edge_nodes;
+  const double* normals;
+  const double* Q;
+  double* offd;
+  double* diag;
+  double* D;
+  double gamma, cfl, delta, eps;
+  int32_t pseudo_time;
+};
+
+// One thread per node: its off-diagonal row blocks, its diagonal block and
+// D_i, accumulated in neighbour order (no atomics, deterministic).
+template <int BS>
+__global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double qi[BS];
+#pragma unroll
+  for (int m = 0; m < BS; ++m) qi[m] = a.Q[(size_t)i * BS + m];
+  double P[BS][BS];
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) P[r][c] = 0.0;
+  double nb[3] = {0.0, 0.0, 0.0};
+  double lsum = 0.0;
+  const int p0 = a.row_ptr[i], p1 = a.row_ptr[i + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = a.col_idx[p];
+    const int e = a.csr_edge[p];
+    const double sg = (a.edge_nodes[2 * e] == i) ? 1.0 : -1.0;
+    const double n[3] = {sg * a.normals[3 * e], sg * a.normals[3 * e + 1], sg * a.normals[3 * e + 2]};
+    nb[0] -= n[0];
+    nb[1] -= n[1];
+    nb[2] -= n[2];
+    double qj[BS], qb[BS];
+#pragma unroll
+    for (int m = 0; m < BS; ++m) {
+      qj[m] = a.Q[(size_t)j * BS + m];
+      qb[m] = 0.5 * (qi[m] + qj[m]);
+    }
+    double M[BS][BS], Aj[BS][BS];
+    abs_flux_jacobian<BS>(qb, n, a.gamma, a.delta, M);
+    flux_jacobian<BS>(qj, n, a.gamma, Aj);
+    double* o = a.offd + (size_t)p * BS * BS;
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        o[r * BS + c] = 0.5 * (Aj[r][c] - M[r][c]);
+        P[r][c] += 0.5 * M[r][c];
+      }
+    lsum += spectral_radius(qb, n, a.gamma);
+  }
+  {
+    double M[BS][BS];
+    abs_flux_jacobian<BS>(qi, nb, a.gamma, a.delta, M);
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int c = 0; c < BS; ++c) P[r][c] += 0.5 * M[r][c];
+    lsum += spectral_radius(qi, nb, a.gamma);
+  }
+  if (BS == 6) P[5][5] *= 2.0;
+  const double scale = a.pseudo_time ? (1.0 + 1.0 / (a.eps * a.cfl)) : 1.0;
+  double* d = a.diag + (size_t)i * BS * BS;
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) d[r * BS + c] = P[r][c] * scale;
+  a.D[i] = a.pseudo_time ? 0.0 : lsum / a.cfl;
+}
+
+// Householder reduction of P_i = J_ii + D_i I to upper Hessenberg form,
+// Q_i^T P_i Q_i = H_i, one thread per node.  Block Jacobi is invariant under
+// the block-diagonal change of basis x = Q x~, and in the new basis every
+// shifted diagonal solve (H_i + i omega V_i I) is O(b^2).
+template <int BS>
+__global__ void __launch_bounds__(128) k_hessenberg(int32_t n, const double* __restrict__ diag,
+                                                    const double* __restrict__ D, double* __restrict__ rot,
+                                                    double* __restrict__ hess, float* __restrict__ hessf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double P[BS][BS], Q[BS][BS];
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      P[r][c] = diag[(size_t)i * BS * BS + r * BS + c];
+      Q[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+#pragma unroll
+  for (int k = 0; k < BS - 2; ++k) {
+    double v[BS];
+    double alpha2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      v[r] = (r > k) ? P[r][k] : 0.0;
+      alpha2 += v[r] * v[r];
+    }
+    if (alpha2 == 0.0) continue;
+    const double alpha = sqrt(alpha2);
+    const double s = (v[k + 1] >= 0.0) ? -alpha : alpha;
+    v[k + 1] -= s;
+    double vn2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < BS; ++r) vn2 += v[r] * v[r];
+    if (vn2 == 0.0) continue;
+    const double beta = 2.0 / vn2;
+    // P <- (I - beta v v^T) P
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int r = 0; r < BS; ++r) t += v[r] * P[r][c];
+      t *= beta;
+#pragma unroll
+      for (int r = 0; r < BS; ++r) P[r][c] -= t * v[r];
+    }
+    // P <- P (I - beta v v^T),  Q <- Q (I - beta v v^T)
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      double t = 0.0, u = 0.0;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        t += P[r][c] * v[c];
+        u += Q[r][c] * v[c];
+      }
+      t *= beta;
+      u *= beta;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        P[r][c] -= t * v[c];
+        Q[r][c] -= u * v[c];
+      }
+    }
+  }
+  const double Di = D[i];
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      const double h = (r > c + 1) ? 0.0 : P[r][c] + (r == c ? Di : 0.0);
+      rot[(size_t)i * BS * BS + r * BS + c] = Q[r][c];
+      hess[(size_t)i * BS * BS + r * BS + c] = h;
+      if (hessf) hessf[(size_t)i * BS * BS + r * BS + c] = (float)h;
+    }
+}
+
+// Rotated off-diagonal blocks Q_i^T J_ij Q_j, one thread per CSR entry (the
+// owning row found by binary search over row_ptr), written in every
+// requested precision (round to nearest).
+template <int BS>
+__global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, const int32_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const double* __restrict__ offd, const double* __restrict__ rot,
+                                                     double* __restrict__ o64, float* __restrict__ o32,
+                                                     __nv_bfloat16* __restrict__ o16) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  int lo = 0, hi = n - 1;  // largest i with row_ptr[i] <= p
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_ptr[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  const int i = lo, j = col_idx[p];
+  double T[BS][BS];
+  const double* J = offd + (size_t)p * BS * BS;
+  const double* Qj = rot + (size_t)j * BS * BS;
+  const double* Qi = rot + (size_t)i * BS * BS;
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < BS; ++k) t += J[r * BS + k] * Qj[k * BS + c];
+      T[r][c] = t;
+    }
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < BS; ++k) t += Qi[k * BS + r] * T[k][c];
+      const size_t o = (size_t)p * BS * BS + r * BS + c;
+      if (o64) o64[o] = t;
+      if (o32) o32[o] = (float)t;
+      if (o16) o16[o] = __double2bfloat16(t);
+    }
+}
+
+template <int BS>
+int launch_build(const BuildArgs& a, cudaStream_t s) {
+  if (a.n == 0) return FNLH_OK;
+  k_build_jacobian<BS><<<(a.n + 127) / 128, 128, 0, s>>>(a);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
+template <int BS>
+int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
+  const PrepLayout L = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
+  double* rot = at<double>(J->prep, L.rot);
+  double* hess = at<double>(J->prep, L.hess);
+  float* hessf = (L.hessf != (size_t)-1) ? at<float>(J->prep, L.hessf) : nullptr;
+  const int n = J->n_nodes;
+  if (n > 0) {
+    k_hessenberg<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf);
+    FNLH_LAUNCH_CHECK();
+  }
+  double* o64 = (L.offd64 != (size_t)-1) ? at<double>(J->prep, L.offd64) : nullptr;
+  float* o32 = (L.offd32 != (size_t)-1) ? at<float>(J->prep, L.offd32) : nullptr;
+  __nv_bfloat16* o16 = (L.offd16 != (size_t)-1) ? at<__nv_bfloat16>(J->prep, L.offd16) : nullptr;
+  if (J->nnz > 0 && (o64 || o32 || o16)) {
+    k_rotate_offd<BS><<<(J->nnz + 127) / 128, 128, 0, s>>>(n, J->nnz, mesh->row_ptr, mesh->col_idx, J->offd, rot,
+                                                         o64, o32, o16);
+    FNLH_LAUNCH_CHECK();
+  }
+  return FNLH_OK;
+}
+
+int build_jacobian_impl(const fnlh_mesh* mesh, const double* Q, const fnlh_params* prm, fnlh_jacobian* J,
+                        cudaStream_t s) {
+  BuildArgs a;
+  a.n = mesh->n_nodes;
+  a.row_ptr = mesh->row_ptr;
+  a.col_idx = mesh->col_idx;
+  a.csr_edge = mesh->csr_edge;
+  a.edge_nodes = mesh->edge_nodes;
+  a.normals = mesh->normals;
+  a.Q = Q;
+  a.offd = J->offd;
+  a.diag = J->diag;
+  a.D = J->D;
+  a.gamma = prm->gamma;
+  a.cfl = prm->cfl;
+  a.delta = prm->entropy_delta;
+  a.eps = prm->eps;
+  a.pseudo_time = prm->pseudo_time;
+  return J->block == 5 ? launch_build<5>(a, s) : launch_build<6>(a, s);
+}
+
+int prepare_impl(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
+  return J->block == 5 ? launch_prepare<5>(mesh, J, s) : launch_prepare<6>(mesh, J, s);
+}
+
+}  // namespace fnlh

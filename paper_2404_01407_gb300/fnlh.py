@@ -1,0 +1,326 @@
+"""ctypes binding of libfnlh.so -- argument marshalling only.
+
+Every function named ``fnlh_*`` here calls the C entry point of the same
+name (declared in include/fnlh.h) with the device pointers of the torch
+tensors it is given and raises :class:`FnlhError` on a non-zero status.  All
+arithmetic of the path runs in the library's CUDA kernels; PyTorch only
+provides device memory and streams.  There is no CPU fallback: without the
+compiled library, :func:`lib` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+c_i32 = ctypes.c_int32
+c_f64 = ctypes.c_double
+c_vp = ctypes.c_void_p
+c_sz = ctypes.c_size_t
+
+FNLH_OK = 0
+FNLH_ERR_ARG = -1
+FNLH_ERR_CUDA = -2
+FNLH_ERR_NONFINITE = -3
+FNLH_ERR_DIVERGED = -4
+FNLH_ERR_TIMEOUT = -5
+FNLH_ERR_UNSUPPORTED = -6
+FNLH_ERR_WORKSPACE = -7
+FNLH_ERR_NOT_CONVERGED = -8
+FNLH_ERR_BAD_MESH = -9
+
+FNLH_F64, FNLH_F32, FNLH_BF16 = 0, 1, 2
+FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16 = 1, 2, 4
+PRECISIONS = {"f64": FNLH_F64, "f32": FNLH_F32, "bf16": FNLH_BF16}
+PREP_FOR = {FNLH_F64: FNLH_PREP_F64, FNLH_F32: FNLH_PREP_F32, FNLH_BF16: FNLH_PREP_BF16}
+MAX_HARMONICS = 64
+
+
+class fnlh_mesh(ctypes.Structure):
+    _fields_ = [("n_nodes", c_i32), ("n_edges", c_i32), ("edge_nodes", c_vp), ("normals", c_vp),
+                ("vol", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("csr_edge", c_vp)]
+
+
+class fnlh_params(ctypes.Structure):
+    _fields_ = [("gamma", c_f64), ("cfl", c_f64), ("entropy_delta", c_f64), ("pseudo_time", c_i32),
+                ("eps", c_f64)]
+
+
+class fnlh_jacobian(ctypes.Structure):
+    _fields_ = [("n_nodes", c_i32), ("nnz", c_i32), ("block", c_i32), ("offd", c_vp), ("diag", c_vp),
+                ("D", c_vp), ("prep", c_vp), ("prep_bytes", c_sz), ("prep_flags", c_i32),
+                ("prep_ready", c_i32)]
+
+
+class fnlh_row(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.POINTER(fnlh_mesh)), ("J", ctypes.POINTER(fnlh_jacobian)),
+                ("n_harm", c_i32), ("omega", ctypes.POINTER(c_f64)), ("B", c_vp), ("X", c_vp)]
+
+
+class fnlh_tuning(ctypes.Structure):
+    _fields_ = [("threads", c_i32), ("ctas_per_sm", c_i32), ("nodes_per_tile", c_i32), ("reserved", c_i32)]
+
+
+class FnlhError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lib().fnlh_strerror(status).decode()} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# C declarations: name -> (restype, argtypes)
+_SIGS = {
+    "fnlh_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "fnlh_version": (ctypes.c_int, []),
+    "fnlh_mesh_build_csr": (ctypes.c_int, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "fnlh_prep_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
+    "fnlh_workspace_bytes": (c_sz, [c_i32, c_i32, c_i32]),
+    "fnlh_build_jacobian": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), c_vp, ctypes.POINTER(fnlh_params),
+                                           ctypes.POINTER(fnlh_jacobian), c_vp]),
+    "fnlh_prepare": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_vp]),
+    "fnlh_relax": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
+                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_i32, c_vp, c_sz, c_vp]),
+    "fnlh_residual": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
+                                     ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "fnlh_solve": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
+                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_f64, c_i32, c_i32, c_vp, c_sz,
+                                  ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_f64), c_vp]),
+    "fnlh_relax_batched": (ctypes.c_int, [ctypes.POINTER(fnlh_row), c_i32, c_i32, c_i32,
+                                          ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
+    "fnlh_batched_extra_bytes": (c_sz, [c_i32]),
+    "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """The loaded libfnlh.so (built in-tree on first use when nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libfnlh.so is not built; the FNLH path has no CPU fallback")
+            h = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = h
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, where: str):
+    if status != FNLH_OK:
+        raise FnlhError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if t.numel() == 0:
+            return None
+        return c_vp(t.data_ptr())
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_vp(stream.cuda_stream)
+
+
+def _omega(omega):
+    arr = np.ascontiguousarray(np.atleast_1d(np.asarray(omega, dtype=np.float64)))
+    if arr.size == 0:
+        arr = np.zeros(1)
+    return arr, arr.ctypes.data_as(ctypes.POINTER(c_f64))
+
+
+# ------------------------------------------------------------------ objects
+
+class DeviceMesh:
+    """Mesh arrays on the device plus the ctypes fnlh_mesh describing them."""
+
+    def __init__(self, n_nodes, edge_nodes, normals, vol, device="cuda"):
+        en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
+        n_edges = en.shape[0]
+        row_ptr = np.zeros(n_nodes + 1, dtype=np.int32)
+        col_idx = np.zeros(max(2 * n_edges, 1), dtype=np.int32)
+        csr_edge = np.zeros(max(2 * n_edges, 1), dtype=np.int32)
+        fnlh_mesh_build_csr(n_nodes, n_edges, en, row_ptr, col_idx, csr_edge)
+        self.n_nodes, self.n_edges = int(n_nodes), int(n_edges)
+        self.row_ptr_host, self.col_idx_host = row_ptr, col_idx[: 2 * n_edges]
+        dev = torch.device(device)
+        self.edge_nodes = torch.from_numpy(en).to(dev)
+        self.normals = torch.from_numpy(np.ascontiguousarray(normals, dtype=np.float64).reshape(-1, 3)).to(dev)
+        self.vol = torch.from_numpy(np.ascontiguousarray(vol, dtype=np.float64)).to(dev)
+        self.row_ptr = torch.from_numpy(row_ptr).to(dev)
+        self.col_idx = torch.from_numpy(col_idx[: 2 * n_edges].copy()).to(dev)
+        self.csr_edge = torch.from_numpy(csr_edge[: 2 * n_edges].copy()).to(dev)
+        self.c = fnlh_mesh(self.n_nodes, self.n_edges, _ptr(self.edge_nodes), _ptr(self.normals), _ptr(self.vol),
+                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.csr_edge))
+
+    @classmethod
+    def from_mesh(cls, mesh, device="cuda"):
+        return cls(mesh.n_nodes, mesh.edge_nodes, mesh.normals, mesh.vol, device)
+
+
+class DeviceJacobian:
+    """J, D and the derived prep blob, all caller-owned torch tensors."""
+
+    def __init__(self, dmesh: DeviceMesh, block: int, prep_flags: int = FNLH_PREP_F64, device="cuda"):
+        n, nnz = dmesh.n_nodes, 2 * dmesh.n_edges
+        dev = torch.device(device)
+        self.block = block
+        self.offd = torch.empty((nnz, block, block), dtype=torch.float64, device=dev)
+        self.diag = torch.empty((n, block, block), dtype=torch.float64, device=dev)
+        self.D = torch.empty((n,), dtype=torch.float64, device=dev)
+        nbytes = fnlh_prep_bytes(n, nnz, block, prep_flags) if prep_flags else 0
+        self.prep = torch.empty((max(nbytes, 1),), dtype=torch.uint8, device=dev) if prep_flags else None
+        self.c = fnlh_jacobian(n, nnz, block, _ptr(self.offd), _ptr(self.diag), _ptr(self.D),
+                               _ptr(self.prep) if self.prep is not None else None, nbytes, prep_flags, 0)
+
+    def nbytes(self):
+        t = self.offd.numel() * 8 + self.diag.numel() * 8 + self.D.numel() * 8
+        return t + (self.prep.numel() if self.prep is not None else 0)
+
+
+def make_params(cfl, gamma=1.4, entropy_delta=0.1, pseudo_time=0, eps=0.6):
+    return fnlh_params(gamma, cfl, entropy_delta, pseudo_time, eps)
+
+
+def workspace(n_nodes, block, n_harm, device="cuda"):
+    nbytes = fnlh_workspace_bytes(n_nodes, block, n_harm)
+    return torch.empty((nbytes,), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------- C entry points
+
+def fnlh_version() -> int:
+    return int(lib().fnlh_version())
+
+
+def fnlh_strerror(status: int) -> str:
+    return lib().fnlh_strerror(status).decode()
+
+
+def fnlh_mesh_build_csr(n_nodes, n_edges, edge_nodes, row_ptr, col_idx, csr_edge):
+    en = np.ascontiguousarray(edge_nodes, dtype=np.int32)
+    st = lib().fnlh_mesh_build_csr(n_nodes, n_edges, en.ctypes.data_as(c_vp), row_ptr.ctypes.data_as(c_vp),
+                                   col_idx.ctypes.data_as(c_vp), csr_edge.ctypes.data_as(c_vp))
+    _check(st, "fnlh_mesh_build_csr")
+
+
+def fnlh_prep_bytes(n_nodes, nnz, block, prep_flags) -> int:
+    return int(lib().fnlh_prep_bytes(n_nodes, nnz, block, prep_flags))
+
+
+def fnlh_workspace_bytes(n_nodes, block, n_harm) -> int:
+    return int(lib().fnlh_workspace_bytes(n_nodes, block, n_harm))
+
+
+def fnlh_build_jacobian(dmesh: DeviceMesh, Q: torch.Tensor, params: fnlh_params, J: DeviceJacobian, stream=None):
+    st = lib().fnlh_build_jacobian(ctypes.byref(dmesh.c), _ptr(Q), ctypes.byref(params), ctypes.byref(J.c),
+                                   _stream(stream))
+    _check(st, "fnlh_build_jacobian")
+
+
+def fnlh_prepare(dmesh: DeviceMesh, J: DeviceJacobian, stream=None):
+    _check(lib().fnlh_prepare(ctypes.byref(dmesh.c), ctypes.byref(J.c), _stream(stream)), "fnlh_prepare")
+
+
+def fnlh_relax(dmesh, J, omega, B, X, sweeps, precision=FNLH_F64, ws=None, stream=None):
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    if ws is None:
+        ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
+    st = lib().fnlh_relax(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), int(sweeps),
+                          int(precision), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fnlh_relax")
+
+
+def fnlh_residual(dmesh, J, omega, B, X, r=None, norms=None, ws=None, stream=None):
+    """Returns the device tensor of norms [K, 2] = (||r_k||^2, ||B_k||^2)."""
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    K = 1 + n_harm
+    if norms is None:
+        norms = torch.empty((K, 2), dtype=torch.float64, device=B.device)
+    if ws is None:
+        ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
+    st = lib().fnlh_residual(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), _ptr(r),
+                             _ptr(norms), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fnlh_residual")
+    return norms
+
+
+def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, ws=None, stream=None,
+               raise_on_error=True):
+    """Returns (status, checks_done, sweeps_done, rel_res[K])."""
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    if ws is None:
+        ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
+    checks, sweeps = c_i32(0), c_i32(0)
+    rel = (c_f64 * (1 + n_harm))()
+    st = lib().fnlh_solve(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), int(precision),
+                          float(tol), int(inner_sweeps), int(max_checks), _ptr(ws), ws.numel(), ctypes.byref(checks),
+                          ctypes.byref(sweeps), rel, _stream(stream))
+    if raise_on_error and st != FNLH_OK:
+        raise FnlhError(st, "fnlh_solve")
+    return st, checks.value, sweeps.value, np.array(rel[:])
+
+
+class BatchedRows:
+    """Holds the ctypes row array (and the omega buffers it points to)."""
+
+    def __init__(self, rows):
+        # rows: list of (dmesh, J, omega, B, X)
+        self.keep = []
+        arr = (fnlh_row * len(rows))()
+        for r, (dm, J, omega, B, X) in enumerate(rows):
+            om, omp = _omega(omega)
+            self.keep.append((dm, J, om, B, X))
+            arr[r] = fnlh_row(ctypes.pointer(dm.c), ctypes.pointer(J.c), len(np.atleast_1d(omega)), omp,
+                              _ptr(B), _ptr(X))
+        self.arr = arr
+        self.n = len(rows)
+
+    def workspace_bytes(self, block):
+        total = int(lib().fnlh_batched_extra_bytes(self.n))
+        for dm, J, om, B, X in self.keep:
+            total += fnlh_workspace_bytes(dm.n_nodes, block, (B.shape[1] - 1) // 2)
+        return total
+
+
+def fnlh_relax_batched(batch: BatchedRows, sweeps, precision, tuning=None, ws=None, stream=None):
+    tn = ctypes.byref(tuning) if tuning is not None else None
+    st = lib().fnlh_relax_batched(batch.arr, batch.n, int(sweeps), int(precision), tn, _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check(st, "fnlh_relax_batched")
+
+
+def fnlh_set_sweep_events(begin=None, end=None):
+    """Record torch.cuda.Event `begin`/`end` around the sweep launches of later calls."""
+    b = c_vp(begin.cuda_event) if begin is not None else None
+    e = c_vp(end.cuda_event) if end is not None else None
+    _check(lib().fnlh_set_sweep_events(b, e), "fnlh_set_sweep_events")

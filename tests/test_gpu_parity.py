@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the FP64 path must match the oracle to relative 1e-12 per system
+(the target the measurement plan states); the Jacobian build to 1e-13 of the
+largest block entry.  The low-precision sweeps are approximations and are
+bounded loosely; the mixed solve must reach a true FP64 relative residual of
+1e-8 (checked with the oracle's residual on the returned x).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_01407_gb300 import fnlh, inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+SMALL = {
+    # ragged sizes: several 256-thread tiles plus a tail
+    "c1": dict(dims=(16, 8, 8), block=5, n_harm=1, cfl=10.0),
+    "b6n4": dict(dims=(20, 12, 10), block=6, n_harm=4, cfl=20.0),
+    "b5n3_ragged": dict(dims=(7, 5, 3), block=5, n_harm=3, cfl=15.0),
+    "b6n0_mean_only": dict(dims=(9, 7, 5), block=6, n_harm=0, cfl=20.0),
+}
+
+
+def small(key, **kw):
+    c = dict(SMALL[key])
+    c.update(kw)
+    return inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c.get("omega_base", 1.0), name=key)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available()
+    fnlh.lib()
+
+
+@pytest.mark.parametrize("key", sorted(SMALL))
+@pytest.mark.parametrize("pseudo", [0, 1])
+def test_build_jacobian_matches_oracle(key, pseudo):
+    p = small(key)
+    dm, J, B = _gpu.device_problem(p, pseudo_time=pseudo)
+    oj = _gpu.oracle_jacobian(p, pseudo_time=pseudo)
+    offd = J.offd.cpu().numpy()
+    diag = J.diag.cpu().numpy()
+    scale = max(np.abs(oj.offd).max(), np.abs(oj.diag).max())
+    assert np.abs(offd - oj.offd).max() <= 1e-13 * scale
+    assert np.abs(diag - oj.diag).max() <= 1e-13 * scale
+    assert np.allclose(J.D.cpu().numpy(), oj.D, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("key", sorted(SMALL))
+def test_relax_f64_isolated_sweep(key):
+    """Oracle J fed to the GPU: only the sweep differs."""
+    p = small(key)
+    dm, J, B = _gpu.device_problem(p)
+    oj = _gpu.oracle_jacobian(p)
+    _gpu.load_jacobian(dm, J, oj)
+    x0 = np.random.default_rng(7).normal(size=p.b.shape)
+    X = torch.from_numpy(x0.copy()).cuda()
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 20, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 20, X0=x0)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("key", sorted(SMALL))
+def test_relax_f64_end_to_end(key):
+    p = small(key)
+    dm, J, B = _gpu.device_problem(p)
+    oj = _gpu.oracle_jacobian(p)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 50, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 50)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+
+
+def test_relax_f64_config2_full_size():
+    """128x64x48, b = 6, mean + 4 harmonics, CFL 20, 50 sweeps: the benchmark's
+    launch configuration, compared with the oracle over the whole mesh."""
+    p = inputs.config_problem("c2")
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F64)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 50, fnlh.FNLH_F64)
+    oj = _gpu.oracle_jacobian(p)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 50)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+    # the build at full size too, sampled rows
+    rows = np.random.default_rng(0).choice(p.mesh.n_nodes, 2000, replace=False)
+    scale = np.abs(oj.diag).max()
+    assert np.abs(J.diag.cpu().numpy()[rows] - oj.diag[rows]).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("key", ["c1", "b6n4", "b6n0_mean_only"])
+def test_residual_matches_oracle(key):
+    p = small(key)
+    dm, J, B = _gpu.device_problem(p)
+    oj = _gpu.oracle_jacobian(p)
+    _gpu.load_jacobian(dm, J, oj)
+    x = np.random.default_rng(3).normal(size=p.b.shape)
+    X = torch.from_numpy(x).cuda()
+    r = torch.empty_like(B)
+    norms = fnlh.fnlh_residual(dm, J, p.omega, B, X, r=r).cpu().numpy()
+    on, orr = oracle.residual(oj, p.mesh.vol, p.omega, p.b, x, want_r=True)
+    assert np.abs(r.cpu().numpy() - orr).max() <= 1e-13 * np.abs(orr).max()
+    assert np.allclose(norms, on, rtol=1e-12, atol=0)
+    # fixed-order reduction: identical bits on a repeat
+    norms2 = fnlh.fnlh_residual(dm, J, p.omega, B, X).cpu().numpy()
+    assert np.array_equal(norms, norms2)
+
+
+@pytest.mark.parametrize("prec,bound", [(fnlh.FNLH_F32, 2e-5), (fnlh.FNLH_BF16, 5e-2)])
+def test_relax_low_precision_bounded(prec, bound):
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    oj = _gpu.oracle_jacobian(p)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 30, prec)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 30)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= bound), err
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_mixed_solve_reaches_1e8(prec):
+    """Defect correction: FP64 residual, low-precision inner sweeps, FP64 update."""
+    p = inputs.problem((32, 24, 16), 6, 8, 20.0, name="c3_reduced")
+    dm, J, B = _gpu.device_problem(p)
+    X = torch.zeros_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    oj = _gpu.oracle_jacobian(p)
+    x = X.cpu().numpy()
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, x)
+    assert np.all(true_rel <= 1.05e-8), true_rel
+    xs, _ = oracle.solve_to_tol(oj, p.mesh.vol, p.omega, p.b, tol=1e-13, chunk=25)
+    err = _gpu.rel_err_per_system(x, xs, p.n_harm)
+    assert np.all(err <= 1e-6), err
+
+
+def test_plain_f64_solve_matches_oracle():
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    X = torch.zeros_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-10, 10, 100)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-10)
+    oj = _gpu.oracle_jacobian(p)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, sweeps)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+
+
+def test_batched_rows_match_per_row():
+    rows = [inputs.problem((9, 7, 5), 6, 2, 20.0, 1.0, seeds=(1, 2, 3)),
+            inputs.problem((12, 8, 6), 6, 8, 20.0, 1.6, seeds=(4, 5, 6)),
+            inputs.problem((10, 9, 7), 6, 4, 20.0, 2.3, seeds=(7, 8, 9))]
+    dev = []
+    for p in rows:
+        dm, J, B = _gpu.device_problem(p)
+        dev.append((p, dm, J, B))
+    singles = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, 13, fnlh.FNLH_F32)
+        singles.append(X.cpu().numpy())
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
+    for tn in (None, fnlh.fnlh_tuning(128, 2, 96, 0)):
+        for X in Xs:
+            X.zero_()
+        fnlh.fnlh_relax_batched(batch, 13, fnlh.FNLH_F32, tuning=tn, ws=ws)
+        for X, ref in zip(Xs, singles):
+            assert np.array_equal(X.cpu().numpy(), ref)
+
+
+def test_single_node_one_sweep_is_exact_block_solve():
+    """No edges: one sweep is the exact shifted block solve (numpy)."""
+    rng = np.random.default_rng(4)
+    mesh = inputs.custom_mesh(np.zeros((1, 3)), np.zeros((0, 2)), vol=[1.7])
+    dm = fnlh.DeviceMesh.from_mesh(mesh)
+    J = fnlh.DeviceJacobian(dm, 6, _gpu.ALL_PREP)
+    P = rng.normal(size=(6, 6)) + 4 * np.eye(6)
+    J.diag.copy_(torch.from_numpy(P[None]))
+    J.D.fill_(0.3)
+    fnlh.fnlh_prepare(dm, J)
+    om = np.array([0.7, 2.0])
+    b = rng.normal(size=(1, 5, 6))
+    B = torch.from_numpy(b).cuda()
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, om, B, X, 1, fnlh.FNLH_F64)
+    x = X.cpu().numpy()
+    ref0 = np.linalg.solve(P + 0.3 * np.eye(6), b[0, 0])
+    assert np.allclose(x[0, 0], ref0, rtol=1e-13, atol=1e-14)
+    for k in (1, 2):
+        M = P + (0.3 + 1j * om[k - 1] * 1.7) * np.eye(6)
+        y = np.linalg.solve(M, b[0, 2 * k - 1] + 1j * b[0, 2 * k])
+        assert np.allclose(x[0, 2 * k - 1] + 1j * x[0, 2 * k], y, rtol=1e-13, atol=1e-14)
+
+
+def test_empty_mesh_is_a_no_op():
+    mesh = inputs.custom_mesh(np.zeros((0, 3)), np.zeros((0, 2)), vol=np.zeros(0))
+    dm = fnlh.DeviceMesh.from_mesh(mesh)
+    J = fnlh.DeviceJacobian(dm, 5, _gpu.ALL_PREP)
+    fnlh.fnlh_build_jacobian(dm, torch.zeros((0, 5), dtype=torch.float64, device="cuda"), fnlh.make_params(10.0), J)
+    B = torch.zeros((0, 3, 5), dtype=torch.float64, device="cuda")
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, [1.0], B, X, 3, fnlh.FNLH_F64)
+    norms = fnlh.fnlh_residual(dm, J, [1.0], B, X).cpu().numpy()
+    assert np.all(norms == 0.0)
+
+
+def test_max_harmonics_and_permuted_numbering():
+    base = inputs.problem((6, 5, 4), 6, 64, 20.0, 0.25)
+    mesh, perm = inputs.permute_mesh(base.mesh, seed=4)
+    p = inputs.Problem(mesh=mesh, q=base.q[perm], b=base.b[perm], omega=base.omega, block=6, cfl=20.0)
+    dm, J, B = _gpu.device_problem(p)
+    oj = _gpu.oracle_jacobian(p)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 25, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 25)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err.max()
+
+
+def test_nonfinite_rhs_is_reported():
+    p = small("c1")
+    dm, J, B = _gpu.device_problem(p)
+    B[3, 1, 2] = float("nan")
+    X = torch.zeros_like(B)
+    st, *_ = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 5, 5, raise_on_error=False)
+    assert st == fnlh.FNLH_ERR_NONFINITE
+
+
+def test_missing_precision_copy_is_reported():
+    p = small("c1")
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F64)
+    X = torch.zeros_like(B)
+    with pytest.raises(fnlh.FnlhError) as e:
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, 2, fnlh.FNLH_BF16)
+    assert e.value.status == fnlh.FNLH_ERR_WORKSPACE
