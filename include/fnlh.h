@@ -219,6 +219,26 @@ int fnlh_relax_batched(const fnlh_row *rows, int32_t n_rows, int32_t sweeps, int
 
 size_t fnlh_batched_extra_bytes(int32_t n_rows);
 
+/* Allocation-free variant of fnlh_residual (the paper has no counterpart).
+ *
+ * Same arguments, results and fixed-order sums as fnlh_residual, minus the
+ * workspace: the per-block partial sums live in a device array built into
+ * the library (1,264,640 bytes on every device that loads it, kept until the
+ * process exits), which covers every valid harmonic count.  It is meant for
+ * callers that cannot allocate device memory -- for instance a host code
+ * whose memory pool owns the whole device budget, or a caller inside a CUDA
+ * stream capture, where cudaMalloc is not allowed -- and therefore cannot
+ * provide the workspace fnlh_residual needs.  The call allocates nothing.
+ * Its first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that may run at the same time on the GPU
+ * (other streams or host threads) race on it and must be serialised by the
+ * caller.  A problem too large for the array (impossible for
+ * n_harm <= FNLH_MAX_HARMONICS) returns FNLH_ERR_UNSUPPORTED. */
+int fnlh_residual_noalloc(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
+                          const double *omega, const double *B, const double *X, double *r,
+                          double *norms, fnlh_stream_t stream);
+
 /* Timing hook (not part of the paper): when both are non-NULL, every later
  * relaxation on this host thread records `begin` on its stream right before
  * its first sweep launch and `end` right after its last one, so that the

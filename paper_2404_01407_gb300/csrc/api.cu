@@ -22,6 +22,8 @@ Systems make_systems(int n_harm, const double* omega);
 int batched_impl(const fnlh_row*, int, int, int, const fnlh_tuning*, void*, size_t, cudaStream_t);
 size_t batched_extra_bytes(int n_rows);
 void set_sweep_events(cudaEvent_t b, cudaEvent_t e);
+int residual_noalloc_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*,
+                            double*, double*, cudaStream_t);
 }  // namespace fnlh
 
 using namespace fnlh;
@@ -241,6 +243,16 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
   if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
   if (workspace_bytes < need) return FNLH_ERR_WORKSPACE;
   return batched_impl(rows, n_rows, sweeps, precision, tuning, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
+                          const double* B, const double* X, double* r, double* norms, fnlh_stream_t stream) {
+  FNLH_TRY(check_mesh(mesh, false));
+  FNLH_TRY(check_jac(mesh, J));
+  FNLH_TRY(check_systems(n_harm, omega));
+  if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
+  const Systems sys = make_systems(n_harm, omega);
+  return residual_noalloc_launch(mesh, J, sys, B, X, r, norms, (cudaStream_t)stream);
 }
 
 int fnlh_set_sweep_events(void* begin, void* end) {

@@ -11,6 +11,8 @@
 // shared memory, and one final pass sums the block partials in block order.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fnlh {
@@ -184,6 +186,74 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   else k_residual<6><<<grid, kResidualThreads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
   k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(a.partials, grid, 2 * sys.K, norms);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
+// ------------------------------------------------------ allocation-free form
+//
+// fnlh_residual_noalloc runs the same two kernels as fnlh_residual, but keeps
+// the per-block partial sums in the file-scope device array below instead of
+// in a workspace the caller allocated.  The array holds the largest grid
+// (kResidualGrid blocks) times two sums for the largest system count
+// (1 + FNLH_MAX_HARMONICS), 1,264,640 bytes, and lives on every device that
+// loads the library until the process exits.  Each call writes every slot it
+// later reads, so nothing has to be cleared between calls; calls share the
+// array, so two calls that may overlap on the GPU (other streams, other host
+// threads) race on it.
+constexpr size_t kNoAllocScratchDoubles = (size_t)kResidualGrid * 2 * kMaxSys;
+static __device__ __align__(256) double g_residual_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The name
+// g_residual_scratch in host code is only a host-side handle, so the address
+// is looked up once per device with that device current and cached.
+static int scratch_address(double** out) {
+  int dev = 0;
+  FNLH_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FNLH_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    double* p = nullptr;
+    FNLH_CUDA_TRY(cudaGetSymbolAddress((void**)&p, g_residual_scratch));
+    if (!p) return FNLH_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return FNLH_OK;
+}
+
+int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
+                            const double* X, double* r, double* norms, cudaStream_t s) {
+  const long long total = (long long)J->n_nodes * sys.K;
+  const long long need = (total + kResidualThreads - 1) / kResidualThreads;
+  const int grid = (int)(need < kResidualGrid ? (need > 0 ? need : 1) : kResidualGrid);
+  if ((size_t)grid * 2 * sys.K > kNoAllocScratchDoubles) return FNLH_ERR_UNSUPPORTED;
+  double* partials = nullptr;
+  const int rc = scratch_address(&partials);
+  if (rc) return rc;
+  ResArgs a;
+  a.n = J->n_nodes;
+  a.row_ptr = m->row_ptr;
+  a.col_idx = m->col_idx;
+  a.offd = J->offd;
+  a.diag = J->diag;
+  a.D = J->D;
+  a.vol = m->vol;
+  a.B = B;
+  a.X = X;
+  a.r = r;
+  a.r32rot = nullptr;
+  a.rot = nullptr;
+  a.partials = partials;
+  a.sys = sys;
+  if (J->block == 5) k_residual<5><<<grid, kResidualThreads, 0, s>>>(a);
+  else k_residual<6><<<grid, kResidualThreads, 0, s>>>(a);
+  FNLH_LAUNCH_CHECK();
+  k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(partials, grid, 2 * sys.K, norms);
   FNLH_LAUNCH_CHECK();
   return FNLH_OK;
 }

@@ -97,6 +97,8 @@ _SIGS = {
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
     "fnlh_batched_extra_bytes": (c_sz, [c_i32]),
     "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
+    "fnlh_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
+                                             ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
 
 
@@ -324,3 +326,18 @@ def fnlh_set_sweep_events(begin=None, end=None):
     b = c_vp(begin.cuda_event) if begin is not None else None
     e = c_vp(end.cuda_event) if end is not None else None
     _check(lib().fnlh_set_sweep_events(b, e), "fnlh_set_sweep_events")
+
+
+def fnlh_residual_noalloc(dmesh, J, omega, B, X, r=None, norms=None, stream=None):
+    """fnlh_residual without a workspace: for callers that cannot allocate
+    device memory (the library keeps the partial sums in its own static device
+    array).  `norms` must be given by such a caller; it is allocated here only
+    as a convenience when omitted."""
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    if norms is None:
+        norms = torch.empty((1 + n_harm, 2), dtype=torch.float64, device=B.device)
+    st = lib().fnlh_residual_noalloc(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X),
+                                     _ptr(r), _ptr(norms), _stream(stream))
+    _check(st, "fnlh_residual_noalloc")
+    return norms
