@@ -1,0 +1,71 @@
+"""Run one operation of one seeded workload a fixed number of times.
+
+A driver for profilers (ncu): it sets the problem up, runs `--warm` untimed
+calls, then `--reps` calls of the chosen operation, and prints their mean
+time from CUDA events.
+
+  python -m paper_2404_01407_gb300.profile_case --op relax --prec bf16 --dims 96 96 64 --harm 8
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import fnlh, inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["relax", "residual", "build", "solve"], default="relax")
+    ap.add_argument("--prec", choices=list(fnlh.PRECISIONS), default="f64")
+    ap.add_argument("--dims", type=int, nargs=3, default=[128, 64, 48])
+    ap.add_argument("--block", type=int, default=6)
+    ap.add_argument("--harm", type=int, default=4)
+    ap.add_argument("--cfl", type=float, default=20.0)
+    ap.add_argument("--sweeps", type=int, default=1)
+    ap.add_argument("--warm", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    prec = fnlh.PRECISIONS[a.prec]
+    p = inputs.problem(tuple(a.dims), a.block, a.harm, a.cfl, name="profile")
+    dev = torch.device("cuda")
+    dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+    J = fnlh.DeviceJacobian(dm, a.block, fnlh.PREP_FOR[prec], dev)
+    Q = torch.from_numpy(p.q).to(dev)
+    params = fnlh.make_params(p.cfl)
+    fnlh.fnlh_build_jacobian(dm, Q, params, J)
+    B = torch.from_numpy(p.b).to(dev)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(p.mesh.n_nodes, a.block, a.harm, dev)
+
+    def op():
+        if a.op == "relax":
+            fnlh.fnlh_relax(dm, J, p.omega, B, X, a.sweeps, prec, ws)
+        elif a.op == "residual":
+            fnlh.fnlh_residual(dm, J, p.omega, B, X, ws=ws)
+        elif a.op == "build":
+            fnlh.fnlh_build_jacobian(dm, Q, params, J)
+        else:
+            X.zero_()
+            fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, a.sweeps, 50, ws=ws)
+
+    for _ in range(a.warm):
+        op()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        op()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": a.op, "prec": a.prec, "dims": a.dims, "harm": a.harm, "nodes": p.mesh.n_nodes,
+                      "ms_per_call": e0.elapsed_time(e1) / max(a.reps, 1),
+                      "finite": bool(np.isfinite(X.cpu().numpy()).all())}))
+
+
+if __name__ == "__main__":
+    main()
