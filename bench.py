@@ -44,16 +44,18 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 NCU_TRAFFIC = {}
 
 
-def hess_solve_flops(b: int, real: bool) -> int:
-    """Flops of one shifted Hessenberg solve (complex, or its real counterpart)."""
+def tri_solve_flops(b: int, real: bool) -> int:
+    """Flops of one shifted back-substitution (T + i s I) y = r with the per-node
+    real Schur factor T: 4 per off-diagonal term and 12 per diagonal division for a
+    complex system; 2 and 2 for the real (mean-flow) system."""
     if real:
-        return 2 * b * (b - 1) + 4 * (b - 1) + b + 1
-    return 8 * b * (b - 1) + 19 * (b - 1) + 6 * b + 5
+        return b * (b - 1) + 2 * b
+    return 2 * b * (b - 1) + 12 * b
 
 
 def sweep_flops(n, nnz, b, n_harm):
     C = 1 + 2 * n_harm
-    return 2.0 * nnz * b * b * C + n * (n_harm * hess_solve_flops(b, False) + hess_solve_flops(b, True))
+    return 2.0 * nnz * b * b * C + n * (n_harm * tri_solve_flops(b, False) + tri_solve_flops(b, True))
 
 
 def sweep_bytes(n, nnz, b, n_harm, s_j, s_d, s_x, s_b):

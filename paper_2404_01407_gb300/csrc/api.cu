@@ -78,6 +78,11 @@ int check_ws(void* ws, size_t bytes, int n, int b, int n_harm, int precision) {
 
 bool valid_precision(int p) { return p == FNLH_F64 || p == FNLH_F32 || p == FNLH_BF16; }
 
+// The sweep kernels index (node, system) pairs with 32-bit arithmetic.
+int check_pairs(int n_nodes, int n_harm) {
+  return ((long long)n_nodes * (1 + n_harm) < (1LL << 31)) ? FNLH_OK : FNLH_ERR_UNSUPPORTED;
+}
+
 }  // namespace
 
 #define FNLH_TRY(expr)       \
@@ -191,6 +196,7 @@ int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   FNLH_TRY(check_prep(J, precision));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
+  FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
   return relax_impl(mesh, J, n_harm, omega, B, X, sweeps, precision, workspace, (cudaStream_t)stream);
 }
 
@@ -220,6 +226,7 @@ int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   FNLH_TRY(check_prep(J, precision));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
+  FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
   return solve_impl(mesh, J, n_harm, omega, B, X, precision, tol, inner_sweeps, max_checks, workspace, checks_done,
                     sweeps_done, rel_res, (cudaStream_t)stream);
 }
@@ -237,6 +244,7 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
     FNLH_TRY(check_systems(R.n_harm, R.omega));
     FNLH_TRY(check_prep(R.J, precision));
     if (R.mesh->n_nodes > 0 && (!R.B || !R.X)) return FNLH_ERR_ARG;
+    FNLH_TRY(check_pairs(R.mesh->n_nodes, R.n_harm));
     need += ws_layout(R.mesh->n_nodes, R.J->block, R.n_harm, precision).total;
   }
   if (!workspace) return FNLH_ERR_WORKSPACE;

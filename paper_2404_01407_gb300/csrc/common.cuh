@@ -36,6 +36,31 @@ template <> __device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv
 }
 template <> __device__ __forceinline__ float ld<float, double>(const double* p) { return (float)__ldg(p); }
 
+// Reciprocal: exact IEEE division in FP64; in FP32 (the inner sweeps of the
+// defect correction, whose result is corrected in FP64 anyway) the
+// hardware approximation, within 2 ulp.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
+// Division by a small runtime constant d without an integer divide:
+// q = (n * m) >> s with m = ceil(2^s / d), s = 31 + ceil(log2 d); exact for
+// every n < 2^31 (the rounding error of m is below 2^-l <= 1/d per unit of n/2^31).
+struct FastDiv {
+  uint32_t d, m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  uint32_t l = 0;
+  while ((1u << l) < d) ++l;
+  f.d = d;
+  f.s = 31 + l;
+  f.m = (uint32_t)(((1ull << f.s) + d - 1) / d);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return (uint32_t)(((uint64_t)n * f.m) >> f.s);
+}
+
 // ----------------------------------------------- shifted Hessenberg solve
 //
 // Solve (H + i s I) y = b for an upper Hessenberg H (row-major BS x BS,
@@ -43,9 +68,32 @@ template <> __device__ __forceinline__ float ld<float, double>(const double* p) 
 // Gaussian elimination with partial pivoting between the two candidate rows
 // of each step (the only rows with a nonzero entry in the pivot column).
 // (yr, yi) holds b on entry and y on return.  Cost O(BS^2) complex
-// operations instead of the O(BS^3) of a general block LU.
+// operations instead of the O(BS^3) of a general block LU.  H may point to
+// global or shared memory (plain loads).
 template <int BS, typename T, typename TH>
 __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr)[BS], T (&yi)[BS]) {
+  // Triangular factor (real Schur form, every subdiagonal exactly zero):
+  // plain back-substitution, y_k = (b_k - sum_{c>k} T_kc y_c) / (T_kk + i s).
+  bool tri = true;
+#pragma unroll
+  for (int k = 0; k < BS - 1; ++k) tri = tri && (H[(k + 1) * BS + k] == TH(0));
+  if (tri) {
+#pragma unroll
+    for (int k = BS - 1; k >= 0; --k) {
+      T ar = yr[k], ai = yi[k];
+#pragma unroll
+      for (int c = k + 1; c < BS; ++c) {
+        const T t = (T)H[k * BS + c];
+        ar -= t * yr[c];
+        ai -= t * yi[c];
+      }
+      const T d = (T)H[k * BS + k];
+      const T inv = recip(d * d + s * s);
+      yr[k] = (ar * d + ai * s) * inv;
+      yi[k] = (ai * d - ar * s) * inv;
+    }
+    return;
+  }
   // upper-triangular factor rows (complex); row k holds columns k..BS-1
   T ur[BS][BS], ui[BS][BS];
   T rr[BS], ri[BS];  // reciprocal of each pivot
@@ -53,7 +101,7 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
   T cr[BS], ci[BS], cbr, cbi;
 #pragma unroll
   for (int c = 0; c < BS; ++c) {
-    cr[c] = ld<T>(H + c);
+    cr[c] = (T)H[c];
     ci[c] = (c == 0) ? s : T(0);
   }
   cbr = yr[0];
@@ -64,30 +112,31 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
     T nr[BS], ni[BS];
 #pragma unroll
     for (int c = k; c < BS; ++c) {
-      nr[c] = ld<T>(H + (k + 1) * BS + c);
+      nr[c] = (T)H[(k + 1) * BS + c];
       ni[c] = (c == k + 1) ? s : T(0);
     }
     T nbr = yr[k + 1], nbi = yi[k + 1];
-    // pivot choice (1-norm magnitude)
-    const bool sw = (fabs(nr[k]) + fabs(ni[k])) > (fabs(cr[k]) + fabs(ci[k]));
+    // pivot choice (1-norm magnitude); on the matrices of this method the
+    // swap is rare, so a branch (uniform over a warp when nobody swaps) is
+    // cheaper than selecting every entry
+    if ((fabs(nr[k]) + fabs(ni[k])) > (fabs(cr[k]) + fabs(ci[k]))) {
 #pragma unroll
-    for (int c = k; c < BS; ++c) {
-      T tr = sw ? nr[c] : cr[c], ti = sw ? ni[c] : ci[c];
-      nr[c] = sw ? cr[c] : nr[c];
-      ni[c] = sw ? ci[c] : ni[c];
-      cr[c] = tr;
-      ci[c] = ti;
-    }
-    {
-      T tr = sw ? nbr : cbr, ti = sw ? nbi : cbi;
-      nbr = sw ? cbr : nbr;
-      nbi = sw ? cbi : nbi;
+      for (int c = k; c < BS; ++c) {
+        const T tr = nr[c], ti = ni[c];
+        nr[c] = cr[c];
+        ni[c] = ci[c];
+        cr[c] = tr;
+        ci[c] = ti;
+      }
+      const T tr = nbr, ti = nbi;
+      nbr = cbr;
+      nbi = cbi;
       cbr = tr;
       cbi = ti;
     }
     // pivot reciprocal
     const T m2 = cr[k] * cr[k] + ci[k] * ci[k];
-    const T inv = T(1) / m2;
+    const T inv = recip(m2);
     rr[k] = cr[k] * inv;
     ri[k] = -ci[k] * inv;
     // store pivot row
@@ -117,7 +166,7 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
   {
     const int k = BS - 1;
     const T m2 = cr[k] * cr[k] + ci[k] * ci[k];
-    const T inv = T(1) / m2;
+    const T inv = recip(m2);
     rr[k] = cr[k] * inv;
     ri[k] = -ci[k] * inv;
     yr[k] = cbr;
@@ -142,7 +191,7 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
 // [0, 256)                      status words (int32)
 // [256, +partials)              residual partial sums  kResidualGrid x 2K doubles
 // norms                         final 2K doubles of the last residual
-// vec0, vec1, vec2              three [n][C][b] vectors in the precision's type
+// vec0, vec1, vec2              three [n][K][b] complex vectors (internal layout) in the precision's type
 struct WsLayout {
   size_t status, partials, norms, vec[3], total, vec_bytes;
 };
@@ -151,13 +200,13 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t precision) {
   WsLayout w;
-  const size_t K = 1 + (size_t)n_harm, C = 1 + 2 * (size_t)n_harm;
+  const size_t K = 1 + (size_t)n_harm;
   const size_t elem = (precision == FNLH_F64) ? 8 : 4;
   w.status = 0;
   w.partials = 256;
   w.norms = w.partials + (size_t)kResidualGrid * 2 * K * sizeof(double);
   size_t off = align256(w.norms + 2 * K * sizeof(double));
-  w.vec_bytes = (size_t)n * C * block * elem;
+  w.vec_bytes = (size_t)n * K * 2 * block * elem;
   for (int v = 0; v < 3; ++v) {
     w.vec[v] = off;
     off = align256(off + w.vec_bytes);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "schur.cuh"
 
 namespace fnlh {
 
@@ -188,77 +189,39 @@ __global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
   a.D[i] = a.pseudo_time ? 0.0 : lsum / a.cfl;
 }
 
-// Householder reduction of P_i = J_ii + D_i I to upper Hessenberg form,
-// Q_i^T P_i Q_i = H_i, one thread per node.  Block Jacobi is invariant under
-// the block-diagonal change of basis x = Q x~, and in the new basis every
-// shifted diagonal solve (H_i + i omega V_i I) is O(b^2).
+// Per-node orthogonal basis for the sweeps, one thread per node:
+// P_i = J_ii + D_i I is reduced to upper Hessenberg form by Householder
+// reflections and then, by the double-shift QR iteration, to real Schur
+// form Z_i^T P_i Z_i = T_i (upper triangular).  Block Jacobi is invariant
+// under the block-diagonal change of basis x = Z x~, and in the new basis the
+// shifted diagonal solve of every system, (T_i + i omega V_i I) y = r, is a
+// back-substitution.  A block whose spectrum has a complex pair keeps the
+// Hessenberg form (the solve then eliminates first).
 template <int BS>
-__global__ void __launch_bounds__(128) k_hessenberg(int32_t n, const double* __restrict__ diag,
-                                                    const double* __restrict__ D, double* __restrict__ rot,
-                                                    double* __restrict__ hess, float* __restrict__ hessf) {
+__global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* __restrict__ diag,
+                                                       const double* __restrict__ D, double* __restrict__ rot,
+                                                       double* __restrict__ hess, float* __restrict__ hessf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double P[BS][BS], Q[BS][BS];
-#pragma unroll
+  const double Di = D[i];
   for (int r = 0; r < BS; ++r)
-#pragma unroll
     for (int c = 0; c < BS; ++c) {
-      P[r][c] = diag[(size_t)i * BS * BS + r * BS + c];
+      P[r][c] = diag[(size_t)i * BS * BS + r * BS + c] + (r == c ? Di : 0.0);
       Q[r][c] = (r == c) ? 1.0 : 0.0;
     }
-#pragma unroll
-  for (int k = 0; k < BS - 2; ++k) {
-    double v[BS];
-    double alpha2 = 0.0;
-#pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      v[r] = (r > k) ? P[r][k] : 0.0;
-      alpha2 += v[r] * v[r];
-    }
-    if (alpha2 == 0.0) continue;
-    const double alpha = sqrt(alpha2);
-    const double s = (v[k + 1] >= 0.0) ? -alpha : alpha;
-    v[k + 1] -= s;
-    double vn2 = 0.0;
-#pragma unroll
-    for (int r = 0; r < BS; ++r) vn2 += v[r] * v[r];
-    if (vn2 == 0.0) continue;
-    const double beta = 2.0 / vn2;
-    // P <- (I - beta v v^T) P
-#pragma unroll
-    for (int c = 0; c < BS; ++c) {
-      double t = 0.0;
-#pragma unroll
-      for (int r = 0; r < BS; ++r) t += v[r] * P[r][c];
-      t *= beta;
-#pragma unroll
-      for (int r = 0; r < BS; ++r) P[r][c] -= t * v[r];
-    }
-    // P <- P (I - beta v v^T),  Q <- Q (I - beta v v^T)
-#pragma unroll
-    for (int r = 0; r < BS; ++r) {
-      double t = 0.0, u = 0.0;
-#pragma unroll
-      for (int c = 0; c < BS; ++c) {
-        t += P[r][c] * v[c];
-        u += Q[r][c] * v[c];
-      }
-      t *= beta;
-      u *= beta;
-#pragma unroll
-      for (int c = 0; c < BS; ++c) {
-        P[r][c] -= t * v[c];
-        Q[r][c] -= u * v[c];
-      }
-    }
-  }
-  const double Di = D[i];
-#pragma unroll
+  hessenberg_reduce<BS>(P, Q);
+  double T[BS][BS], Z[BS][BS];
   for (int r = 0; r < BS; ++r)
-#pragma unroll
     for (int c = 0; c < BS; ++c) {
-      const double h = (r > c + 1) ? 0.0 : P[r][c] + (r == c ? Di : 0.0);
-      rot[(size_t)i * BS * BS + r * BS + c] = Q[r][c];
+      T[r][c] = P[r][c];
+      Z[r][c] = Q[r][c];
+    }
+  const bool tri = schur_real<BS>(T, Z);
+  for (int r = 0; r < BS; ++r)
+    for (int c = 0; c < BS; ++c) {
+      const double h = tri ? ((r > c) ? 0.0 : T[r][c]) : ((r > c + 1) ? 0.0 : P[r][c]);
+      rot[(size_t)i * BS * BS + r * BS + c] = tri ? Z[r][c] : Q[r][c];
       hess[(size_t)i * BS * BS + r * BS + c] = h;
       if (hessf) hessf[(size_t)i * BS * BS + r * BS + c] = (float)h;
     }
@@ -325,7 +288,7 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   float* hessf = (L.hessf != (size_t)-1) ? at<float>(J->prep, L.hessf) : nullptr;
   const int n = J->n_nodes;
   if (n > 0) {
-    k_hessenberg<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf);
+    k_prepare_basis<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf);
     FNLH_LAUNCH_CHECK();
   }
   double* o64 = (L.offd64 != (size_t)-1) ? at<double>(J->prep, L.offd64) : nullptr;

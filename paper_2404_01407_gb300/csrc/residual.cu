@@ -28,7 +28,7 @@ struct ResArgs {
   const double* B;
   const double* X;
   double* r;        // nullable [n][C][b]
-  float* r32rot;    // nullable [n][C][b]: Q_i^T r_i rounded to FP32
+  float* r32rot;    // nullable [n][K][b] complex: Q_i^T r_i rounded to FP32
   const double* rot;
   double* partials; // [gridDim][2K]
   Systems sys;
@@ -120,8 +120,10 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
         }
       }
       if (a.r32rot) {
+        // Q_i^T r in the sweeps' internal layout [n][K][b] complex (the mean
+        // flow's imaginary part is written as an exact zero)
         const double* Q = a.rot + (size_t)i * BS * BS;
-        float* rp = a.r32rot + ((size_t)i * C + c0) * BS;
+        float* rp = a.r32rot + ((size_t)i * K + k) * 2 * BS;
 #pragma unroll
         for (int q = 0; q < BS; ++q) {
           double ar = 0.0, ai = 0.0;
@@ -131,8 +133,8 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
             ar += qv * rr[t];
             ai += qv * ri[t];
           }
-          rp[q] = (float)ar;
-          if (cplx) rp[BS + q] = (float)ai;
+          rp[2 * q] = (float)ar;
+          rp[2 * q + 1] = cplx ? (float)ai : 0.0f;
         }
       }
     }

@@ -6,13 +6,13 @@
 // J across all systems:
 //   x_i <- (J_ii + (D_i + i omega_k V_i) I)^-1 (B_i - sum_j J_ij x_j).
 //
-// Design (GB300): one thread per (node, system).  Each thread streams the
-// node's off-diagonal blocks (shared by the node's K threads through L1),
-// gathers the neighbours' Re/Im columns of its system, accumulates the
-// off-diagonal product in registers and solves its shifted diagonal system
-// in registers.  The sweeps run in the per-node Hessenberg basis prepared by
+// Design (GB300): one thread per (node, system); the off-diagonal product is
+// accumulated in registers and the shifted diagonal system solved in
+// registers.  The sweeps run in the per-node Hessenberg basis prepared by
 // fnlh_prepare (x = Q x~), where the diagonal block of system k is
-// H_i + i omega_k V_i I and the solve costs O(b^2).
+// H_i + i omega_k V_i I and its solve costs O(b^2).  Iterates live in the
+// internal complex-interleaved layout [n][K][b]; the rotate kernels move
+// between it and the caller's [n][C][b] layout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,68 +23,98 @@
 
 namespace fnlh {
 
+constexpr int kSweepThreads = 256;
+
 struct SweepArgs {
-  int32_t n;
-  const int32_t* row_ptr;
-  const int32_t* col_idx;
-  const void* offd;  // rotated blocks, TJ
-  const void* hess;  // [n][b][b] T
-  const double* vol;
-  const void* Bt;    // [n][C][b] T, rotated right-hand side
-  const void* Xin;   // [n][C][b] T (not read when x_zero)
-  void* Xout;        // [n][C][b] T
+  TileRow row;
   int32_t x_zero;
-  Systems sys;
+  int32_t smem_floats;
+  int32_t* status;  // workspace status word (bit 0: a bounded wait timed out)
+  double omega[kMaxSys];
 };
 
-template <int BS, typename TJ, typename T>
-__global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs a) {
+// FP64: one thread per pair, blocks from global memory.
+template <int BS>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = a.sys.K;
-  if (g >= (long long)a.n * K) return;
-  const int i = (int)(g / K);
-  const int k = (int)(g - (long long)i * K);
-  sweep_pair<BS, TJ, T>(a.row_ptr, a.col_idx, (const TJ*)a.offd, (const T*)a.hess, a.vol, (const T*)a.Bt,
-                        (const T*)a.Xin, (T*)a.Xout, a.sys.C, i, k, a.sys.omega[k], a.x_zero != 0);
+  if (g >= (long long)a.row.n * a.row.K) return;
+  TileRow R = a.row;
+  R.omega = a.omega;
+  sweep_pair_f64<BS>(R, g, a.x_zero != 0);
 }
 
-// y_i[c] = Q_i^T x_i[c]  (into the Hessenberg basis), one thread per (node, column).
+// FP32 arithmetic on FP32 or BF16 blocks, staged per CTA tile.
+template <int BS, typename TJ>
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_f32(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  TileRow R = a.row;
+  R.omega = a.omega;
+  sweep_tile_f32<BS, TJ>(R, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
+}
+
+// Caller layout [n][C][b] (FP64) -> internal [n][K][b] complex, y = Q_i^T x,
+// one thread per (node, system).
 template <int BS, typename TO>
-__global__ void __launch_bounds__(256) k_rotate_in(long long count, int C, const double* __restrict__ rot,
+__global__ void __launch_bounds__(256) k_rotate_in(long long count, int K, const double* __restrict__ rot,
                                                    const double* __restrict__ x, TO* __restrict__ y) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= count) return;
-  const long long i = g / C;
+  const long long i = g / K;
+  const int k = (int)(g - i * K);
+  const int C = 2 * K - 1;
   const double* Q = rot + i * BS * BS;
-  double v[BS];
+  const double* xr = x + (i * C + (k == 0 ? 0 : 2 * k - 1)) * BS;
+  double vr[BS], vi[BS];
 #pragma unroll
-  for (int t = 0; t < BS; ++t) v[t] = x[g * BS + t];
+  for (int t = 0; t < BS; ++t) {
+    vr[t] = xr[t];
+    vi[t] = (k == 0) ? 0.0 : xr[BS + t];
+  }
+  TO* out = y + g * 2 * BS;
 #pragma unroll
   for (int r = 0; r < BS; ++r) {
-    double acc = 0.0;
+    double ar = 0.0, ai = 0.0;
 #pragma unroll
-    for (int t = 0; t < BS; ++t) acc += Q[t * BS + r] * v[t];
-    y[g * BS + r] = (TO)acc;
+    for (int t = 0; t < BS; ++t) {
+      const double q = __ldg(Q + t * BS + r);
+      ar += q * vr[t];
+      ai += q * vi[t];
+    }
+    out[2 * r] = (TO)ar;
+    out[2 * r + 1] = (TO)ai;
   }
 }
 
-// x_i[c] (+)= Q_i y_i[c]  (back to the original basis, FP64), one thread per (node, column).
+// Internal [n][K][b] complex -> caller layout (FP64), x (+)= Q_i y.
 template <int BS, typename TI>
-__global__ void __launch_bounds__(256) k_rotate_out(long long count, int C, const double* __restrict__ rot,
+__global__ void __launch_bounds__(256) k_rotate_out(long long count, int K, const double* __restrict__ rot,
                                                     const TI* __restrict__ y, double* __restrict__ x, int accumulate) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= count) return;
-  const long long i = g / C;
+  const long long i = g / K;
+  const int k = (int)(g - i * K);
+  const int C = 2 * K - 1;
   const double* Q = rot + i * BS * BS;
-  double v[BS];
+  const TI* in = y + g * 2 * BS;
+  double vr[BS], vi[BS];
 #pragma unroll
-  for (int t = 0; t < BS; ++t) v[t] = (double)y[g * BS + t];
+  for (int t = 0; t < BS; ++t) {
+    vr[t] = (double)in[2 * t];
+    vi[t] = (double)in[2 * t + 1];
+  }
+  double* xr = x + (i * C + (k == 0 ? 0 : 2 * k - 1)) * BS;
 #pragma unroll
   for (int r = 0; r < BS; ++r) {
-    double acc = accumulate ? x[g * BS + r] : 0.0;
+    double ar = accumulate ? xr[r] : 0.0, ai = 0.0;
+    if (k > 0 && accumulate) ai = xr[BS + r];
 #pragma unroll
-    for (int t = 0; t < BS; ++t) acc += Q[r * BS + t] * v[t];
-    x[g * BS + r] = acc;
+    for (int t = 0; t < BS; ++t) {
+      const double q = __ldg(Q + r * BS + t);
+      ar += q * vr[t];
+      ai += q * vi[t];
+    }
+    xr[r] = ar;
+    if (k > 0) xr[BS + r] = ai;
   }
 }
 
@@ -93,29 +123,19 @@ static inline unsigned blocks_for(long long count, int threads) {
 }
 
 template <int BS, typename TO>
-int rotate_in(int n, int C, const double* rot, const double* x, TO* y, cudaStream_t s) {
-  const long long count = (long long)n * C;
+int rotate_in(int n, int K, const double* rot, const double* x, TO* y, cudaStream_t s) {
+  const long long count = (long long)n * K;
   if (count == 0) return FNLH_OK;
-  k_rotate_in<BS, TO><<<blocks_for(count, 256), 256, 0, s>>>(count, C, rot, x, y);
+  k_rotate_in<BS, TO><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rot, x, y);
   FNLH_LAUNCH_CHECK();
   return FNLH_OK;
 }
 
 template <int BS, typename TI>
-int rotate_out(int n, int C, const double* rot, const TI* y, double* x, int accumulate, cudaStream_t s) {
-  const long long count = (long long)n * C;
+int rotate_out(int n, int K, const double* rot, const TI* y, double* x, int accumulate, cudaStream_t s) {
+  const long long count = (long long)n * K;
   if (count == 0) return FNLH_OK;
-  k_rotate_out<BS, TI><<<blocks_for(count, 256), 256, 0, s>>>(count, C, rot, y, x, accumulate);
-  FNLH_LAUNCH_CHECK();
-  return FNLH_OK;
-}
-
-template <int BS, typename TJ, typename T>
-int sweep_launch(const SweepArgs& a, int threads, cudaStream_t s) {
-  const long long count = (long long)a.n * a.sys.K;
-  if (count == 0) return FNLH_OK;
-  if (threads <= 0) threads = 256;
-  k_sweep<BS, TJ, T><<<blocks_for(count, threads), threads, 0, s>>>(a);
+  k_rotate_out<BS, TI><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rot, y, x, accumulate);
   FNLH_LAUNCH_CHECK();
   return FNLH_OK;
 }
@@ -165,30 +185,65 @@ static inline int mark(cudaEvent_t ev, cudaStream_t s) {
   return FNLH_OK;
 }
 
+constexpr size_t kMaxStageBytes = 200 * 1024;
+
+// Dynamic shared memory of a staged launch; tiles that need more than this
+// fall back to unstaged loads inside the kernel.
+template <typename KernelT>
+int stage_setup(KernelT kernel, int threads, int K, int BS, int* floats, size_t* bytes) {
+  size_t b = (size_t)stage_floats(threads, K, BS) * sizeof(float);
+  b = std::min(b, kMaxStageBytes);
+  *floats = (int)(b / sizeof(float));
+  *bytes = b;
+  if (b > 48 * 1024) FNLH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+  return FNLH_OK;
+}
+
+template <int BS, typename TJ, typename T>
+int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
+  const long long count = (long long)a.row.n * a.row.K;
+  if (count == 0) return FNLH_OK;
+  if constexpr (sizeof(T) == 8) {
+    k_sweep_f64<BS><<<blocks_for(count, kSweepThreads), kSweepThreads, 0, s>>>(a);
+  } else {
+    k_sweep_f32<BS, TJ><<<blocks_for(count, kSweepThreads), kSweepThreads, smem_bytes, s>>>(a);
+  }
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
 // Runs `sweeps` sweeps between the ping-pong buffers x0/x1 starting from x0
 // (or from zero when x_zero), returns the buffer holding the result.
 template <int BS, typename TJ, typename T>
 int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, const T* Bt, T* x0, T* x1,
-               int sweeps, int x_zero, int threads, cudaStream_t s, T** result) {
+               int sweeps, int x_zero, int32_t* status, cudaStream_t s, T** result) {
   SweepArgs a;
-  a.n = m->n_nodes;
-  a.row_ptr = m->row_ptr;
-  a.col_idx = m->col_idx;
-  a.offd = op.offd;
-  a.hess = op.hess;
-  a.vol = m->vol;
-  a.Bt = Bt;
-  a.sys = sys;
+  std::memset(&a, 0, sizeof(a));
+  a.row.n = m->n_nodes;
+  a.row.K = sys.K;
+  a.row.divK = make_fastdiv((uint32_t)sys.K);
+  a.row.row_ptr = m->row_ptr;
+  a.row.col_idx = m->col_idx;
+  a.row.offd = op.offd;
+  a.row.hess = op.hess;
+  a.row.vol = m->vol;
+  a.row.Bt = Bt;
+  a.status = status;
+  for (int k = 0; k < kMaxSys; ++k) a.omega[k] = sys.omega[k];
+  size_t smem = 0;
+  int rc = FNLH_OK;
+  if constexpr (sizeof(T) == 4) {
+    rc = stage_setup(k_sweep_f32<BS, TJ>, kSweepThreads, sys.K, BS, &a.smem_floats, &smem);
+    if (rc) return rc;
+  }
   T* cur = x0;
   T* nxt = x1;
-  int rc = mark(g_ev_begin, s);
-  if (rc) return rc;
+  if ((rc = mark(g_ev_begin, s))) return rc;
   for (int it = 0; it < sweeps; ++it) {
-    a.Xin = cur;
-    a.Xout = nxt;
+    a.row.Xin = cur;
+    a.row.Xout = nxt;
     a.x_zero = (it == 0) ? x_zero : 0;
-    rc = sweep_launch<BS, TJ, T>(a, threads, s);
-    if (rc) return rc;
+    if ((rc = sweep_launch<BS, TJ, T>(a, smem, s))) return rc;
     T* t = cur;
     cur = nxt;
     nxt = t;
@@ -209,11 +264,12 @@ int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   T* x0 = at<T>(ws, W.vec[1]);
   T* x1 = at<T>(ws, W.vec[2]);
   const int n = J->n_nodes;
-  if ((rc = rotate_in<BS, T>(n, sys.C, op.rot, B, bt, s))) return rc;
-  if ((rc = rotate_in<BS, T>(n, sys.C, op.rot, X, x0, s))) return rc;
+  if ((rc = rotate_in<BS, T>(n, sys.K, op.rot, B, bt, s))) return rc;
+  if ((rc = rotate_in<BS, T>(n, sys.K, op.rot, X, x0, s))) return rc;
   T* res = x0;
-  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, 0, s, &res))) return rc;
-  return rotate_out<BS, T>(n, sys.C, op.rot, res, X, 0, s);
+  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, at<int32_t>(ws, W.status), s, &res)))
+    return rc;
+  return rotate_out<BS, T>(n, sys.K, op.rot, res, X, 0, s);
 }
 
 int relax_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
@@ -239,7 +295,7 @@ struct Check {
   double first_max;
 };
 
-// Evaluates the residual, copies the norms to the host and classifies them.
+// Classifies the residual norms copied to the host.
 static int check_norms(const double* hn, int K, double tol, Check* ck, bool first, bool* converged) {
   double worst = 0.0;
   bool finite = true;
@@ -267,6 +323,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   const WsLayout W = ws_layout(J->n_nodes, BS, n_harm, precision);
   const int n = J->n_nodes, K = sys.K;
   double* norms = at<double>(ws, W.norms);
+  int32_t* status = at<int32_t>(ws, W.status);
   T* v0 = at<T>(ws, W.vec[0]);
   T* v1 = at<T>(ws, W.vec[1]);
   T* v2 = at<T>(ws, W.vec[2]);
@@ -277,28 +334,35 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   const bool mixed = precision != FNLH_F64;
   if (!mixed) {
     // plain FP64 Jacobi: iterate in the rotated basis, check every `inner` sweeps
-    if ((rc = rotate_in<BS, T>(n, sys.C, op.rot, B, v0, s))) return rc;
-    if ((rc = rotate_in<BS, T>(n, sys.C, op.rot, X, v1, s))) return rc;
+    if ((rc = rotate_in<BS, T>(n, K, op.rot, B, v0, s))) return rc;
+    if ((rc = rotate_in<BS, T>(n, K, op.rot, X, v1, s))) return rc;
   }
   T* cur = v1;
+  FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   for (;;) {
     rc = residual_launch(m, J, sys, B, X, nullptr, mixed ? (float*)v0 : nullptr, op.rot, norms, ws, s);
     if (rc) return rc;
+    int32_t hstatus = 0;
     FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
+    FNLH_CUDA_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hstatus) {
+      rc = FNLH_ERR_TIMEOUT;
+      break;
+    }
     rc = check_norms(hn, K, tol, &ck, checks == 0, &conv);
     ++checks;
     if (rc || conv || checks >= max_checks) break;
     T* res = nullptr;
     if (mixed) {
       // inner: A~ e = r~ from e = 0 (v1/v2 ping-pong), then x += Q e in FP64
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, 0, s, &res))) return rc;
-      if ((rc = rotate_out<BS, T>(n, sys.C, op.rot, res, X, 1, s))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res))) return rc;
+      if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 1, s))) return rc;
     } else {
       T* other = (cur == v1) ? v2 : v1;
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, 0, s, &res))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res))) return rc;
       cur = res;
-      if ((rc = rotate_out<BS, T>(n, sys.C, op.rot, res, X, 0, s))) return rc;
+      if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 0, s))) return rc;
     }
     sweeps += inner;
   }
@@ -328,50 +392,45 @@ int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const dou
 
 // ----------------------------------------------------------- batched rows
 //
-// Several blade rows (different meshes, block counts and harmonic counts) in
-// one persistent launch per sweep.  The (node, system) pairs of every row are
-// cut into tiles of `tile_pairs` consecutive pairs; a grid of
-// SMs x ctas_per_sm CTAs walks the global tile list round-robin, so the
-// rows' tails share one launch instead of each paying its own.  The row
-// descriptors travel as a __grid_constant__ kernel parameter (no device
-// memory, capturable in a CUDA graph).
+// Several blade rows (different meshes and harmonic counts) in one
+// persistent launch per sweep.  The (node, system) pairs of every row are cut
+// into tiles of blockDim.x consecutive pairs; a grid of SMs x ctas_per_sm
+// CTAs walks the global tile list round-robin, so the rows share one launch
+// and one tail instead of each paying its own.  The row descriptors travel as
+// a __grid_constant__ kernel parameter (no device memory, capturable in a
+// CUDA graph).
 
 constexpr int kMaxBatchRows = 8;
 
 struct BatchRow {
-  int32_t n, K, C, pad;
-  long long tile0;  // first global tile of this row
-  long long pairs;  // n K
-  const int32_t* row_ptr;
-  const int32_t* col_idx;
-  const void* offd;
-  const void* hess;
-  const double* vol;
-  const void* Bt;
-  void* x[2];       // ping-pong iterate buffers
+  TileRow row;
+  void* x[2];        // ping-pong iterate buffers
+  long long tile0;   // first global tile of this row
   double omega[kMaxSys];
 };
 
 struct BatchArgs {
-  int32_t n_rows, parity, x_zero, tile_pairs;
+  int32_t n_rows, parity, smem_floats, pad;
   long long n_tiles;
   BatchRow row[kMaxBatchRows];
 };
 
 template <int BS, typename TJ, typename T>
-__global__ void __launch_bounds__(256) k_sweep_batched(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) float smem[];
   for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
     int r = 0;
     while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
-    const BatchRow& R = a.row[r];
-    const long long first = (t - R.tile0) * a.tile_pairs;
-    for (int q = threadIdx.x; q < a.tile_pairs; q += blockDim.x) {
-      const long long g = first + q;
-      if (g >= R.pairs) break;
-      const int i = (int)(g / R.K);
-      const int k = (int)(g - (long long)i * R.K);
-      sweep_pair<BS, TJ, T>(R.row_ptr, R.col_idx, (const TJ*)R.offd, (const T*)R.hess, R.vol, (const T*)R.Bt,
-                            (const T*)R.x[a.parity], (T*)R.x[a.parity ^ 1], R.C, i, k, R.omega[k], a.x_zero != 0);
+    TileRow R = a.row[r].row;
+    R.omega = a.row[r].omega;
+    R.Xin = a.row[r].x[a.parity];
+    R.Xout = a.row[r].x[a.parity ^ 1];
+    const long long g0 = (t - a.row[r].tile0) * blockDim.x;
+    if constexpr (sizeof(T) == 8) {
+      const long long g = g0 + threadIdx.x;
+      if (g < (long long)R.n * R.K) sweep_pair_f64<BS>(R, g, false);
+    } else {
+      sweep_tile_f32<BS, TJ>(R, g0, false, smem, a.smem_floats);
     }
   }
 }
@@ -383,17 +442,16 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
                   cudaStream_t s) {
   static thread_local BatchArgs a;  // large: kept off the stack (the launch copies it)
   std::memset(&a, 0, sizeof(a));
-  int threads = (tn && tn->threads > 0) ? tn->threads : 256;
-  int ctas_per_sm = (tn && tn->ctas_per_sm > 0) ? tn->ctas_per_sm : 4;
-  int tile_pairs = (tn && tn->nodes_per_tile > 0) ? tn->nodes_per_tile : threads;
-  if (threads > 256 || threads % 32) return FNLH_ERR_ARG;
+  const int threads = (tn && tn->threads > 0) ? tn->threads : kSweepThreads;
+  const int ctas_per_sm = (tn && tn->ctas_per_sm > 0) ? tn->ctas_per_sm : 4;
+  if (threads > kSweepThreads || threads % 32) return FNLH_ERR_ARG;
   int dev = 0, sms = 0;
   FNLH_CUDA_TRY(cudaGetDevice(&dev));
   FNLH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   size_t off = 256;
   long long tiles = 0;
+  int kmin = kMaxSys;
   a.n_rows = n_rows;
-  a.tile_pairs = tile_pairs;
   SweepOperands ops[kMaxBatchRows];
   for (int r = 0; r < n_rows; ++r) {
     const fnlh_row& R = rows[r];
@@ -404,25 +462,30 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
     char* base = (char*)ws + off;
     off += W.total;
     BatchRow& D = a.row[r];
-    D.n = R.mesh->n_nodes;
-    D.K = sys.K;
-    D.C = sys.C;
-    D.pairs = (long long)D.n * D.K;
-    D.tile0 = tiles;
-    tiles += (D.pairs + tile_pairs - 1) / tile_pairs;
-    D.row_ptr = R.mesh->row_ptr;
-    D.col_idx = R.mesh->col_idx;
-    D.offd = ops[r].offd;
-    D.hess = ops[r].hess;
-    D.vol = R.mesh->vol;
-    D.Bt = base + W.vec[0];
+    D.row.n = R.mesh->n_nodes;
+    D.row.K = sys.K;
+    D.row.divK = make_fastdiv((uint32_t)sys.K);
+    D.row.row_ptr = R.mesh->row_ptr;
+    D.row.col_idx = R.mesh->col_idx;
+    D.row.offd = ops[r].offd;
+    D.row.hess = ops[r].hess;
+    D.row.vol = R.mesh->vol;
+    D.row.Bt = base + W.vec[0];
     D.x[0] = base + W.vec[1];
     D.x[1] = base + W.vec[2];
+    D.tile0 = tiles;
+    tiles += ((long long)D.row.n * D.row.K + threads - 1) / threads;
+    kmin = std::min(kmin, sys.K);
     for (int k = 0; k < kMaxSys; ++k) D.omega[k] = sys.omega[k];
-    if ((rc = rotate_in<BS, T>(D.n, D.C, ops[r].rot, R.B, (T*)D.Bt, s))) return rc;
-    if ((rc = rotate_in<BS, T>(D.n, D.C, ops[r].rot, R.X, (T*)D.x[0], s))) return rc;
+    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.B, (T*)D.row.Bt, s))) return rc;
+    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.X, (T*)D.x[0], s))) return rc;
   }
   a.n_tiles = tiles;
+  size_t smem = 0;
+  if constexpr (sizeof(T) == 4) {
+    int rc = stage_setup(k_sweep_batched<BS, TJ, T>, threads, kmin, BS, &a.smem_floats, &smem);
+    if (rc) return rc;
+  }
   const long long grid_ll = std::min<long long>(tiles, (long long)sms * ctas_per_sm);
   const unsigned grid = (unsigned)std::max<long long>(grid_ll, 1);
   {
@@ -431,9 +494,8 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   }
   for (int it = 0; it < sweeps; ++it) {
     a.parity = it & 1;
-    a.x_zero = 0;
     if (tiles > 0) {
-      k_sweep_batched<BS, TJ, T><<<grid, threads, 0, s>>>(a);
+      k_sweep_batched<BS, TJ, T><<<grid, threads, smem, s>>>(a);
       FNLH_LAUNCH_CHECK();
     }
   }
@@ -444,7 +506,7 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   const int fin = sweeps & 1;
   for (int r = 0; r < n_rows; ++r) {
     const BatchRow& D = a.row[r];
-    int rc = rotate_out<BS, T>(D.n, D.C, ops[r].rot, (const T*)D.x[fin], rows[r].X, 0, s);
+    int rc = rotate_out<BS, T>(D.row.n, D.row.K, ops[r].rot, (const T*)D.x[fin], rows[r].X, 0, s);
     if (rc) return rc;
   }
   return FNLH_OK;

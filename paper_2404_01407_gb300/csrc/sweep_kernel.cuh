@@ -1,61 +1,288 @@
-// Per-(node, system) body of the block-Jacobi sweep, shared by the single-row
-// and the batched multi-row kernels.
+// Body of the block-Jacobi sweep, shared by the single-row and the batched
+// multi-row kernels.
+//
+// One thread per (node, system).  The iterate and right-hand side use the
+// library's internal layout [n][K][b] of complex (re, im) pairs in the
+// per-node Hessenberg basis (the mean flow, system 0, carries a zero
+// imaginary part), so each thread's slice is one contiguous vector.
+//
+// A CTA owns a tile of consecutive (node, system) pairs.  In the staged form
+// (low-precision blocks, FP32 arithmetic) the CTA first copies the
+// off-diagonal blocks and Hessenberg factors of its nodes into shared memory
+// with coalesced vector loads, converting them to FP32 once, instead of each
+// of a node's K threads loading every block entry itself.
 #pragma once
 
 #include "common.cuh"
 
 namespace fnlh {
 
-// x_i <- (H_i + i omega_k V_i I)^-1 (B~_i - sum_j J~_ij x_j) for the columns of
-// system k (column 0 for the mean flow, 2k-1 / 2k for harmonic k), all in the
-// per-node Hessenberg basis.  The mean flow goes through the same complex
-// code with a zero imaginary part, so every lane of a warp runs the same
-// instructions.
-template <int BS, typename TJ, typename T>
-__device__ __forceinline__ void sweep_pair(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                                           const TJ* __restrict__ offd, const T* __restrict__ hess,
-                                           const double* __restrict__ vol, const T* __restrict__ Bt,
-                                           const T* __restrict__ Xin, T* __restrict__ Xout, int C, int i, int k,
-                                           double omega_k, bool x_zero) {
-  const int c0 = (k == 0) ? 0 : 2 * k - 1;
-  const bool cplx = k > 0;
-  T sr[BS], si[BS];
-  const T* bi = Bt + ((size_t)i * C + c0) * BS;
+// ---------------------------------------------------------- vector access
+
+template <int BS, typename T>
+struct Cvec {
+  T re[BS], im[BS];
+};
+
+// Load / store the (re, im) interleaved slice of BS complex values.
+template <int BS>
+__device__ __forceinline__ void load_slice(const float* __restrict__ p, Cvec<BS, float>& v) {
+  if constexpr ((2 * BS) % 4 == 0) {
 #pragma unroll
-  for (int r = 0; r < BS; ++r) {
-    sr[r] = bi[r];
-    si[r] = cplx ? bi[BS + r] : T(0);
+    for (int q = 0; q < BS / 2; ++q) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+      v.re[2 * q] = f.x;
+      v.im[2 * q] = f.y;
+      v.re[2 * q + 1] = f.z;
+      v.im[2 * q + 1] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      const float2 f = __ldg(reinterpret_cast<const float2*>(p) + q);
+      v.re[q] = f.x;
+      v.im[q] = f.y;
+    }
   }
-  if (!x_zero) {
-    const int p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
-    for (int p = p0; p < p1; ++p) {
-      const int j = __ldg(col_idx + p);
-      const T* xj = Xin + ((size_t)j * C + c0) * BS;
-      T xr[BS], xi[BS];
+}
+
+template <int BS>
+__device__ __forceinline__ void load_slice(const double* __restrict__ p, Cvec<BS, double>& v) {
 #pragma unroll
-      for (int t = 0; t < BS; ++t) {
-        xr[t] = xj[t];
-        xi[t] = cplx ? xj[BS + t] : T(0);
-      }
-      const TJ* J = offd + (size_t)p * BS * BS;
+  for (int q = 0; q < BS; ++q) {
+    const double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
+    v.re[q] = f.x;
+    v.im[q] = f.y;
+  }
+}
+
+template <int BS>
+__device__ __forceinline__ void store_slice(float* __restrict__ p, const Cvec<BS, float>& v) {
+  if constexpr ((2 * BS) % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < BS / 2; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v.re[2 * q], v.im[2 * q], v.re[2 * q + 1], v.im[2 * q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < BS; ++q) reinterpret_cast<float2*>(p)[q] = make_float2(v.re[q], v.im[q]);
+  }
+}
+
+template <int BS>
+__device__ __forceinline__ void store_slice(double* __restrict__ p, const Cvec<BS, double>& v) {
+#pragma unroll
+  for (int q = 0; q < BS; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v.re[q], v.im[q]);
+}
+
+// Load one BS x BS block into registers (row-major).
+template <int BS>
+__device__ __forceinline__ void load_block(const double* __restrict__ p, double (&J)[BS * BS]) {
+  if constexpr ((BS * BS) % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < BS * BS / 2; ++q) {
+      const double2 f = __ldg(reinterpret_cast<const double2*>(p) + q);
+      J[2 * q] = f.x;
+      J[2 * q + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < BS * BS; ++q) J[q] = __ldg(p + q);
+  }
+}
+
+// FP32 block from shared memory (staged) or global memory.
+template <int BS>
+__device__ __forceinline__ void load_block_f32(const float* p, float (&J)[BS * BS]) {
+  if constexpr ((BS * BS) % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < BS * BS / 4; ++q) {
+      const float4 f = reinterpret_cast<const float4*>(p)[q];
+      J[4 * q] = f.x;
+      J[4 * q + 1] = f.y;
+      J[4 * q + 2] = f.z;
+      J[4 * q + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < BS * BS; ++q) J[q] = p[q];
+  }
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// ------------------------------------------------------------ staging
+
+// Copy `count` FP32 values from global src to shared dst (both 16-byte
+// aligned when count is a multiple of 4), all threads of the CTA.
+__device__ __forceinline__ void stage_f32(float* __restrict__ dst, const float* __restrict__ src, int count,
+                                          bool vec4) {
+  if (vec4) {
+    const int n4 = count >> 2;
+    for (int q = threadIdx.x; q < n4; q += blockDim.x)
+      reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+  } else {
+    for (int q = threadIdx.x; q < count; q += blockDim.x) dst[q] = __ldg(src + q);
+  }
+}
+
+// Copy `count` BF16 values to shared memory as FP32 (8-byte chunks when
+// the source is 8-byte aligned and count a multiple of 4).
+__device__ __forceinline__ void stage_bf16(float* __restrict__ dst, const __nv_bfloat16* __restrict__ src, int count,
+                                           bool vec4) {
+  if (vec4) {
+    const int n4 = count >> 2;
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+      const uint2 w = __ldg(reinterpret_cast<const uint2*>(src) + q);
+      reinterpret_cast<float4*>(dst)[q] = make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
+    }
+  } else {
+    const uint16_t* s = reinterpret_cast<const uint16_t*>(src);
+    for (int q = threadIdx.x; q < count; q += blockDim.x) dst[q] = __uint_as_float((uint32_t)__ldg(s + q) << 16);
+  }
+}
+
+// Shared-memory floats needed by a staged tile of `threads` pairs: the
+// tile's blocks, factors and neighbour indices.
+__host__ __device__ inline int stage_cap_nodes(int threads, int K) { return (threads + K - 1) / K + 1; }
+constexpr int kStageDegree = 7;  // blocks per node the stage buffer is sized for (hex meshes: <= 6)
+__host__ __device__ inline int stage_floats(int threads, int K, int BS) {
+  const int nodes = stage_cap_nodes(threads, K);
+  return (nodes * kStageDegree + nodes) * BS * BS + nodes * kStageDegree;
+}
+
+// ------------------------------------------------------------ the tile
+
+struct TileRow {
+  int32_t n, K;
+  FastDiv divK;      // division by K (pair index -> node), n K < 2^31
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* offd;  // rotated off-diagonal blocks (TJ)
+  const void* hess;  // [n][b][b] (double for FP64 sweeps, float otherwise)
+  const double* vol;
+  const void* Bt;    // [n][K][b] complex, right-hand side in the rotated basis
+  const void* Xin;   // [n][K][b] complex (not read when x_zero)
+  void* Xout;
+  const double* omega;  // [K], omega[0] = 0
+};
+
+// Shifted Hessenberg solve + store for one pair, shared by both forms.
+template <int BS, typename T, typename TH>
+__device__ __forceinline__ void finish_pair(const TileRow& R, const TH* H, int i, int k, Cvec<BS, T>& s) {
+  const T shift = (T)(R.omega[k] * __ldg(R.vol + i));
+  hess_solve<BS, T>(H, shift, s.re, s.im);
+  store_slice<BS>((T*)R.Xout + ((size_t)i * R.K + k) * 2 * BS, s);
+}
+
+// FP64 (or unstaged) form: blocks and factors straight from global memory.
+template <int BS>
+__device__ __forceinline__ void sweep_pair_f64(const TileRow& R, long long g, bool x_zero) {
+  const int i = (int)fdiv((uint32_t)g, R.divK);
+  const int k = (int)g - i * R.K;
+  Cvec<BS, double> s;
+  load_slice<BS>((const double*)R.Bt + ((size_t)i * R.K + k) * 2 * BS, s);
+  if (!x_zero) {
+    const double* __restrict__ X = (const double*)R.Xin;
+    const double* __restrict__ offd = (const double*)R.offd;
+    const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
+    for (int p = p0; p < p1; ++p) {
+      const int j = __ldg(R.col_idx + p);
+      Cvec<BS, double> x;
+      load_slice<BS>(X + ((size_t)j * R.K + k) * 2 * BS, x);
+      double J[BS * BS];
+      load_block<BS>(offd + (size_t)p * BS * BS, J);
 #pragma unroll
       for (int r = 0; r < BS; ++r)
 #pragma unroll
         for (int t = 0; t < BS; ++t) {
-          const T jv = ld<T>(J + r * BS + t);
-          sr[r] -= jv * xr[t];
-          si[r] -= jv * xi[t];
+          s.re[r] -= J[r * BS + t] * x.re[t];
+          s.im[r] -= J[r * BS + t] * x.im[t];
         }
     }
   }
-  const T s = (T)(omega_k * __ldg(vol + i));
-  hess_solve<BS, T>(hess + (size_t)i * BS * BS, s, sr, si);
-  T* xo = Xout + ((size_t)i * C + c0) * BS;
-#pragma unroll
-  for (int r = 0; r < BS; ++r) {
-    xo[r] = sr[r];
-    if (cplx) xo[BS + r] = si[r];
+  finish_pair<BS, double>(R, (const double*)R.hess + (size_t)i * BS * BS, i, k, s);
+}
+
+// Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
+// Every thread of the CTA must call it (it synchronises).
+// Every thread of the CTA must call this (it synchronises).
+template <int BS, typename TJ>
+__device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, bool x_zero, float* smem,
+                                               int smem_floats) {
+  const uint32_t total = (uint32_t)R.n * (uint32_t)R.K;
+  const uint32_t gs = (uint32_t)g0;
+  const uint32_t g = gs + threadIdx.x;
+  const int i_first = (int)fdiv(gs, R.divK);
+  const uint32_t g_last = min(gs + blockDim.x, total) - 1;
+  const int i_last = (int)fdiv(g_last, R.divK);
+  const int nodes = i_last - i_first + 1;
+  const int p_first = __ldg(R.row_ptr + i_first), p_end = __ldg(R.row_ptr + i_last + 1);
+  const int nblk = x_zero ? 0 : (p_end - p_first);
+  // blocks, factors and neighbour indices of the tile (uniform over the CTA)
+  const bool staged = (nblk + nodes) * BS * BS + nblk <= smem_floats;
+  float* sJ = smem;
+  float* sH = smem + nblk * BS * BS;
+  int* sC = reinterpret_cast<int*>(sH + nodes * BS * BS);
+  if (staged) {
+    const bool v4 = ((BS * BS) % 4 == 0);
+    if (nblk > 0) {
+      if constexpr (sizeof(TJ) == 2)
+        stage_bf16(sJ, (const __nv_bfloat16*)R.offd + (size_t)p_first * BS * BS, nblk * BS * BS, v4);
+      else
+        stage_f32(sJ, (const float*)R.offd + (size_t)p_first * BS * BS, nblk * BS * BS, v4);
+      for (int q = threadIdx.x; q < nblk; q += blockDim.x) sC[q] = __ldg(R.col_idx + p_first + q);
+    }
+    stage_f32(sH, (const float*)R.hess + (size_t)i_first * BS * BS, nodes * BS * BS, v4);
   }
+  __syncthreads();
+  if (g < total) {
+    const int i = (int)fdiv(g, R.divK);
+    const int k = (int)g - i * R.K;
+    Cvec<BS, float> s;
+    load_slice<BS>((const float*)R.Bt + (size_t)g * 2 * BS, s);
+    if (!x_zero) {
+      const float* __restrict__ Xk = (const float*)R.Xin + (size_t)k * 2 * BS;
+      const size_t stride = (size_t)R.K * 2 * BS;
+      const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
+      // software pipeline: the next neighbour's slice is in flight while the
+      // current one is multiplied
+      Cvec<BS, float> xn;
+      if (p0 < p1) {
+        const int j = staged ? sC[p0 - p_first] : __ldg(R.col_idx + p0);
+        load_slice<BS>(Xk + (size_t)j * stride, xn);
+      }
+      for (int p = p0; p < p1; ++p) {
+        const Cvec<BS, float> x = xn;
+        if (p + 1 < p1) {
+          const int j = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
+          load_slice<BS>(Xk + (size_t)j * stride, xn);
+        }
+        float J[BS * BS];
+        if (staged) {
+          load_block_f32<BS>(sJ + (size_t)(p - p_first) * BS * BS, J);
+        } else if constexpr (sizeof(TJ) == 2) {
+          const uint16_t* q = reinterpret_cast<const uint16_t*>(R.offd) + (size_t)p * BS * BS;
+#pragma unroll
+          for (int e = 0; e < BS * BS; ++e) J[e] = __uint_as_float((uint32_t)__ldg(q + e) << 16);
+        } else {
+          const float* q = (const float*)R.offd + (size_t)p * BS * BS;
+#pragma unroll
+          for (int e = 0; e < BS * BS; ++e) J[e] = __ldg(q + e);
+        }
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) {
+            s.re[r] -= J[r * BS + t] * x.re[t];
+            s.im[r] -= J[r * BS + t] * x.im[t];
+          }
+      }
+    }
+    const float* H = staged ? sH + (size_t)(i - i_first) * BS * BS : (const float*)R.hess + (size_t)i * BS * BS;
+    finish_pair<BS, float>(R, H, i, k, s);
+  }
+  __syncthreads();  // the stage buffer is reused by the next tile
 }
 
 }  // namespace fnlh

@@ -57,14 +57,24 @@ def main():
         op()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
+    for b, e in sw:  # torch creates the CUDA event on its first record
+        b.record()
+        e.record()
     e0.record()
-    for _ in range(a.reps):
+    for r in range(a.reps):
+        if a.op == "relax":
+            fnlh.fnlh_set_sweep_events(*sw[r])
         op()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"op": a.op, "prec": a.prec, "dims": a.dims, "harm": a.harm, "nodes": p.mesh.n_nodes,
-                      "ms_per_call": e0.elapsed_time(e1) / max(a.reps, 1),
-                      "finite": bool(np.isfinite(X.cpu().numpy()).all())}))
+    fnlh.fnlh_set_sweep_events(None, None)
+    out = {"op": a.op, "prec": a.prec, "dims": a.dims, "harm": a.harm, "nodes": p.mesh.n_nodes,
+           "ms_per_call": e0.elapsed_time(e1) / max(a.reps, 1),
+           "finite": bool(np.isfinite(X.cpu().numpy()).all())}
+    if a.op == "relax" and a.reps > 0 and a.sweeps > 0:
+        out["ms_per_sweep"] = sum(b.elapsed_time(e) for b, e in sw) / (a.reps * a.sweeps)
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -244,3 +244,38 @@ def test_missing_precision_copy_is_reported():
     with pytest.raises(fnlh.FnlhError) as e:
         fnlh.fnlh_relax(dm, J, p.omega, B, X, 2, fnlh.FNLH_BF16)
     assert e.value.status == fnlh.FNLH_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F64, fnlh.FNLH_F32])
+def test_complex_spectrum_block_uses_hessenberg_fallback(prec):
+    """Diagonal blocks whose spectrum has a complex pair keep the Hessenberg
+    form; one sweep from zero must still be the exact shifted block solve."""
+    rng = np.random.default_rng(8)
+    mesh = inputs.custom_mesh(np.zeros((2, 3)), np.zeros((0, 2)), vol=[1.3, 0.7])
+    dm = fnlh.DeviceMesh.from_mesh(mesh)
+    J = fnlh.DeviceJacobian(dm, 6, _gpu.ALL_PREP)
+    Ps = []
+    for node in range(2):
+        V = rng.normal(size=(6, 6)) + 3 * np.eye(6)
+        Dm = np.diag(rng.uniform(2, 4, 6))
+        if node == 0:
+            Dm[1:3, 1:3] = [[2.5, 1.5], [-1.5, 2.5]]  # eigenvalues 2.5 +- 1.5i
+        Ps.append(V @ Dm @ np.linalg.inv(V))
+    J.diag.copy_(torch.from_numpy(np.stack(Ps)))
+    J.D.zero_()
+    fnlh.fnlh_prepare(dm, J)
+    om = np.array([0.9, 2.2, 3.1])
+    b = rng.normal(size=(2, 7, 6))
+    B = torch.from_numpy(b).cuda()
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, om, B, X, 1, prec)
+    x = X.cpu().numpy()
+    tol = 1e-12 if prec == fnlh.FNLH_F64 else 1e-5
+    for node in range(2):
+        ref0 = np.linalg.solve(Ps[node], b[node, 0])
+        assert np.linalg.norm(x[node, 0] - ref0) <= tol * np.linalg.norm(ref0)
+        for k in (1, 2, 3):
+            M = Ps[node] + 1j * om[k - 1] * mesh.vol[node] * np.eye(6)
+            y = np.linalg.solve(M, b[node, 2 * k - 1] + 1j * b[node, 2 * k])
+            got = x[node, 2 * k - 1] + 1j * x[node, 2 * k]
+            assert np.linalg.norm(got - y) <= tol * np.linalg.norm(y)
