@@ -416,7 +416,7 @@ struct BatchArgs {
 };
 
 template <int BS, typename TJ, typename T>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) float smem[];
   for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
     int r = 0;

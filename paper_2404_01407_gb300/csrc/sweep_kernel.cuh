@@ -113,32 +113,101 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 
 // ------------------------------------------------------------ staging
 
-// Copy `count` FP32 values from global src to shared dst (both 16-byte
-// aligned when count is a multiple of 4), all threads of the CTA.
+// Staging copies global -> shared, all threads of the CTA.  Each thread
+// first issues a batch of kStageBatch independent loads into registers and
+// only then converts and stores them, so that a batch costs one memory
+// latency instead of one per element.
+constexpr int kStageBatch = 8;
+
+// `count` FP32 values (16-byte chunks when vec4: both pointers 16-byte
+// aligned and count a multiple of 4).
 __device__ __forceinline__ void stage_f32(float* __restrict__ dst, const float* __restrict__ src, int count,
                                           bool vec4) {
   if (vec4) {
     const int n4 = count >> 2;
-    for (int q = threadIdx.x; q < n4; q += blockDim.x)
-      reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+    for (int base = 0; base < n4; base += kStageBatch * blockDim.x) {
+      float4 w[kStageBatch];
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < n4) w[u] = __ldg(reinterpret_cast<const float4*>(src) + q);
+      }
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < n4) reinterpret_cast<float4*>(dst)[q] = w[u];
+      }
+    }
   } else {
-    for (int q = threadIdx.x; q < count; q += blockDim.x) dst[q] = __ldg(src + q);
+    for (int base = 0; base < count; base += kStageBatch * blockDim.x) {
+      float w[kStageBatch];
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < count) w[u] = __ldg(src + q);
+      }
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < count) dst[q] = w[u];
+      }
+    }
   }
 }
 
-// Copy `count` BF16 values to shared memory as FP32 (8-byte chunks when
-// the source is 8-byte aligned and count a multiple of 4).
+// `count` BF16 values to shared memory as FP32 (8-byte chunks when the
+// source is 8-byte aligned and count a multiple of 4).
 __device__ __forceinline__ void stage_bf16(float* __restrict__ dst, const __nv_bfloat16* __restrict__ src, int count,
                                            bool vec4) {
   if (vec4) {
     const int n4 = count >> 2;
-    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-      const uint2 w = __ldg(reinterpret_cast<const uint2*>(src) + q);
-      reinterpret_cast<float4*>(dst)[q] = make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
+    for (int base = 0; base < n4; base += kStageBatch * blockDim.x) {
+      uint2 w[kStageBatch];
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < n4) w[u] = __ldg(reinterpret_cast<const uint2*>(src) + q);
+      }
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < n4)
+          reinterpret_cast<float4*>(dst)[q] =
+              make_float4(bf16_lo(w[u].x), bf16_hi(w[u].x), bf16_lo(w[u].y), bf16_hi(w[u].y));
+      }
     }
   } else {
     const uint16_t* s = reinterpret_cast<const uint16_t*>(src);
-    for (int q = threadIdx.x; q < count; q += blockDim.x) dst[q] = __uint_as_float((uint32_t)__ldg(s + q) << 16);
+    for (int base = 0; base < count; base += kStageBatch * blockDim.x) {
+      uint32_t w[kStageBatch];
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < count) w[u] = __ldg(s + q);
+      }
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) {
+        const int q = base + u * blockDim.x + threadIdx.x;
+        if (q < count) dst[q] = __uint_as_float(w[u] << 16);
+      }
+    }
+  }
+}
+
+// `count` int32 values.
+__device__ __forceinline__ void stage_i32(int* __restrict__ dst, const int* __restrict__ src, int count) {
+  for (int base = 0; base < count; base += kStageBatch * blockDim.x) {
+    int w[kStageBatch];
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int q = base + u * blockDim.x + threadIdx.x;
+      if (q < count) w[u] = __ldg(src + q);
+    }
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int q = base + u * blockDim.x + threadIdx.x;
+      if (q < count) dst[q] = w[u];
+    }
   }
 }
 
@@ -224,6 +293,9 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, b
   float* sJ = smem;
   float* sH = smem + nblk * BS * BS;
   int* sC = reinterpret_cast<int*>(sH + nodes * BS * BS);
+  // the right-hand side slice is loaded first, so that it is in flight during the staging
+  Cvec<BS, float> s;
+  if (g < total) load_slice<BS>((const float*)R.Bt + (size_t)g * 2 * BS, s);
   if (staged) {
     const bool v4 = ((BS * BS) % 4 == 0);
     if (nblk > 0) {
@@ -231,7 +303,7 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, b
         stage_bf16(sJ, (const __nv_bfloat16*)R.offd + (size_t)p_first * BS * BS, nblk * BS * BS, v4);
       else
         stage_f32(sJ, (const float*)R.offd + (size_t)p_first * BS * BS, nblk * BS * BS, v4);
-      for (int q = threadIdx.x; q < nblk; q += blockDim.x) sC[q] = __ldg(R.col_idx + p_first + q);
+      stage_i32(sC, R.col_idx + p_first, nblk);
     }
     stage_f32(sH, (const float*)R.hess + (size_t)i_first * BS * BS, nodes * BS * BS, v4);
   }
@@ -239,8 +311,6 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, b
   if (g < total) {
     const int i = (int)fdiv(g, R.divK);
     const int k = (int)g - i * R.K;
-    Cvec<BS, float> s;
-    load_slice<BS>((const float*)R.Bt + (size_t)g * 2 * BS, s);
     if (!x_zero) {
       const float* __restrict__ Xk = (const float*)R.Xin + (size_t)k * 2 * BS;
       const size_t stride = (size_t)R.K * 2 * BS;
