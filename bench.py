@@ -336,6 +336,9 @@ def run_fnlh(args):
         line["mixed_vs_fp64"] = mixed_section(torch, fnlh, inputs, dev)
         torch.cuda.empty_cache()
         line["batched"] = batched_section(torch, fnlh, inputs, dev, args)
+        if not args.no_large:
+            torch.cuda.empty_cache()
+            line["large"] = large_section(torch, fnlh, inputs, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(p)
     if rank == 0:
@@ -358,14 +361,13 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
     ws = fnlh.workspace(n, b, N, dev)
     out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, b=6, mean + {N} harmonics, CFL 20, tol {tol:g}"}
     cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 12)]
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
     for name, prec, inner in cases:
-        X.zero_()
-        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False)  # warm
-        X.zero_()
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)  # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=ws,
-                                                  raise_on_error=False)
+                                                  raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         out[name] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
@@ -373,6 +375,79 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
     if out["f64"]["status"] == "success":
         for name in ("f32", "bf16"):
             out[name]["speedup_vs_f64"] = out["f64"]["seconds"] / out[name]["seconds"]
+    # the inner sweep alone: HBM roofline (algorithmic bytes, FP32 iterate)
+    peaks, _ = load_peaks()
+    nnz = 2 * p.mesh.n_edges
+    for name, prec, sj in (("f32", fnlh.FNLH_F32, 4), ("bf16", fnlh.FNLH_BF16, 2)):
+        ms = sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec)
+        alg = sweep_bytes(n, nnz, b, N, sj, 4, 4, 4)
+        out[name]["inner_sweep"] = {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
+                                    "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec, sweeps=10, reps=3):
+    """Average duration of one sweep launch (CUDA events recorded by the library around its sweep launches)."""
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 2, prec, ws)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, z in ev:
+        a.record()
+        z.record()
+    for a, z in ev:
+        fnlh.fnlh_set_sweep_events(a, z)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec, ws)
+    torch.cuda.synchronize()
+    fnlh.fnlh_set_sweep_events(None, None)
+    return sum(a.elapsed_time(z) for a, z in ev) / (reps * sweeps)
+
+
+def large_section(torch, fnlh, inputs, dev, tol=1e-8):
+    """c5: 256x200x156 (8M nodes), b=6, mean + 16 harmonics, BF16 blocks with FP64 defect correction;
+    Jacobian bytes for N=1 and N=16; peak device memory."""
+    c = inputs.CONFIGS["c5"]
+    mesh = inputs.hex_mesh(*c["dims"])
+    q = inputs.flow_state(mesh.n_nodes, 6)
+    n = mesh.n_nodes
+    dm = fnlh.DeviceMesh.from_mesh(mesh, dev)
+    J = fnlh.DeviceJacobian(dm, 6, fnlh.FNLH_PREP_BF16, dev)
+    fnlh.fnlh_build_jacobian(dm, torch.from_numpy(q).to(dev), fnlh.make_params(c["cfl"]), J)
+    del q
+    out = {"workload": f"c5: 256x200x156 hex passage, {n} nodes, {mesh.n_edges} edges, b=6, CFL {c['cfl']:g}, "
+                       f"BF16 blocks, FP64 defect correction to {tol:g}",
+           "jacobian_bytes": J.nbytes()}
+    peaks, _ = load_peaks()
+    for N in (16, 1):
+        torch.cuda.reset_peak_memory_stats(dev)
+        Bh = inputs.rhs(n, 6, N)
+        B = torch.from_numpy(Bh).to(dev)
+        del Bh
+        X = torch.empty_like(B)
+        ws = fnlh.workspace(n, 6, N, dev, precision=fnlh.FNLH_BF16)
+        om = inputs.omegas(N)
+        zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+        fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 12, 1, ws=ws, raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 12, 200, ws=ws,
+                                                  raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+
+        class _P:
+            omega = om
+        ms = sweep_time_ms(torch, fnlh, dm, J, _P, B, X, ws, fnlh.FNLH_BF16)
+        alg = sweep_bytes(n, 2 * mesh.n_edges, 6, N, 2, 4, 4, 4)
+        out[f"N{N}"] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
+                        "max_rel_residual": float(np.max(rel)), "jacobian_bytes": J.nbytes(),
+                        "workspace_bytes": ws.numel(), "vector_bytes": 2 * B.numel() * 8,
+                        "updates_per_s": n * (1 + N) * sweeps / t,
+                        "inner_sweep": {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
+                                        "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                        "peak_device_bytes": torch.cuda.max_memory_allocated(dev)}
+        del B, X, ws
+        torch.cuda.empty_cache()
+    out["jacobian_bytes_independent_of_N"] = out["N1"]["jacobian_bytes"] == out["N16"]["jacobian_bytes"]
     return out
 
 
@@ -387,7 +462,8 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         J = fnlh.DeviceJacobian(dm, p.block, fnlh.PREP_FOR[prec], dev)
         fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
         B = torch.from_numpy(p.b).to(dev)
-        rows.append((p, dm, J, B, torch.zeros_like(B), fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev)))
+        rows.append((p, dm, J, B, torch.zeros_like(B),
+                     fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev, precision=prec)))
     updates = sum(p.mesh.n_nodes * (1 + p.n_harm) for p, *_ in rows) * sweeps
 
     def per_row():
@@ -429,8 +505,7 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
     t_graph = timeit(g.replay)
     return {"workload": "c4: rows 80x50x50 (N=2), 100x75x80 (N=8), 125x110x80 (N=4), b=6, "
                         f"{sweeps} {prec_name} sweeps", "per_row_ms": t_rows, "batched_ms": t_batch,
-            "batched_graph_ms": t_graph, "tuning": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm,
-                                                    "tile_pairs": best.nodes_per_tile},
+            "batched_graph_ms": t_graph, "tuning": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm},
             "updates_per_s_graph": updates / (t_graph * 1e-3), "speedup_vs_per_row": t_rows / t_graph,
             "tuning_table": table}
 
@@ -443,6 +518,7 @@ def main():
     ap.add_argument("--impl", default="fnlh", choices=["fnlh", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -124,12 +124,11 @@ typedef struct fnlh_row {
     double *X;           /* [n][C][b] in: x0, out: x */
 } fnlh_row;
 
-/* Launch shape of the sweep kernels (0 = library default). */
+/* Launch shape of the batched sweep kernel (0 = library default). */
 typedef struct fnlh_tuning {
-    int32_t threads;      /* threads per CTA */
-    int32_t ctas_per_sm;  /* persistent grid = SMs x this */
-    int32_t nodes_per_tile; /* nodes per work tile of the batched kernel */
-    int32_t reserved;
+    int32_t threads;      /* threads per CTA = (node, system) pairs per tile; 32..256, multiple of 32 */
+    int32_t ctas_per_sm;  /* 0: one CTA per tile; > 0: persistent grid of SMs x this CTAs */
+    int32_t reserved[2];
 } fnlh_tuning;
 
 /* Human-readable text of a status code (static storage). */
@@ -148,8 +147,10 @@ int fnlh_mesh_build_csr(int32_t n_nodes, int32_t n_edges, const int32_t *edge_no
 /* Bytes of the derived blob for fnlh_prepare. */
 size_t fnlh_prep_bytes(int32_t n_nodes, int32_t nnz, int32_t block, int32_t prep_flags);
 
-/* Bytes of scratch space any call below needs for this problem size. */
-size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm);
+/* Bytes of scratch space the calls below need for this problem size when
+ * they run at `precision` (FNLH_F64 gives the largest size, enough for any
+ * precision; fnlh_residual alone needs the FNLH_F32 size).  0 on bad input. */
+size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision);
 
 /* Assemble J (off-diagonal and diagonal blocks) and D from the conservative
  * state Q [n][b] (rho, rho u, rho v, rho w, rho E[, rho nu]) -- the
@@ -192,11 +193,15 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
                   const double *omega, const double *B, const double *X, double *r,
                   double *norms, void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
 
+/* fnlh_solve flags */
+#define FNLH_SOLVE_ZERO_GUESS 1 /* start from x0 = 0 (X is overwritten; the first residual is B) */
+
 /* Solve every system to ||r_k|| <= tol ||B_k||.  precision FNLH_F64: plain FP64
  * Jacobi with an FP64 residual check every `inner_sweeps` sweeps.
  * FNLH_F32 / FNLH_BF16: defect correction -- FP64 residual r = B - A x,
  * `inner_sweeps` sweeps on A e = r with the low-precision blocks and FP32
- * arithmetic from e = 0, then x += e in FP64; repeated.  X: in x0, out x.
+ * arithmetic from e = 0 (r and e rotated in FP32), then x += e with the sum in
+ * FP64; repeated.  X: in x0 (ignored with FNLH_SOLVE_ZERO_GUESS), out x.
  * SYNCHRONISING (reads the norms after every check).  Outputs (host, each
  * nullable): *checks_done residual evaluations, *sweeps_done total sweeps,
  * rel_res [K] final ||r_k||/||B_k||.  Returns FNLH_ERR_NOT_CONVERGED after
@@ -204,13 +209,14 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
  * non-finite or growing (x1e3) residual. */
 int fnlh_solve(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
                const double *B, double *X, int32_t precision, double tol, int32_t inner_sweeps,
-               int32_t max_checks, void *workspace, size_t workspace_bytes, int32_t *checks_done,
-               int32_t *sweeps_done, double *rel_res, fnlh_stream_t stream);
+               int32_t max_checks, int32_t flags, void *workspace, size_t workspace_bytes,
+               int32_t *checks_done, int32_t *sweeps_done, double *rel_res, fnlh_stream_t stream);
 
 /* Batched form: `sweeps` sweeps of fnlh_relax on several blade rows of
  * different sizes and harmonic counts (the multi-row FNLH setting of the
- * paper's Results) with one persistent kernel launch per sweep over a tile
- * list spanning every row.  tuning may be NULL (defaults).  workspace: at
+ * paper's Results) with one kernel launch per sweep over a tile list
+ * spanning every row (one CTA per tile, or a persistent grid).  At most 8
+ * rows, all with the same block size.  tuning may be NULL (defaults).  workspace: at
  * least the sum of fnlh_workspace_bytes of the rows plus
  * fnlh_batched_extra_bytes(n_rows).  Asynchronous, graph-capturable. */
 int fnlh_relax_batched(const fnlh_row *rows, int32_t n_rows, int32_t sweeps, int32_t precision,

@@ -1,8 +1,8 @@
 """Autotuner for the launch shape of the batched persistent sweep.
 
-Searches threads per CTA, CTAs per SM (persistent grid size) and the tile
-length (consecutive (node, system) pairs per work tile) by timing the real
-kernel with CUDA events, and caches the winner per problem signature
+Searches threads per CTA (= (node, system) pairs per tile) and the grid shape
+(one CTA per tile, or a persistent grid of SMs x ctas_per_sm CTAs) by timing
+the real kernel with CUDA events, and caches the winner per problem signature
 (block size, per-row systems, node-count bucket, precision, SM count) in a
 JSON file next to the library (git-ignored).
 """
@@ -18,8 +18,7 @@ from . import fnlh
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 SEARCH_THREADS = (128, 256)
-SEARCH_CTAS_PER_SM = (2, 4, 8)
-SEARCH_TILE_MULT = (1, 2, 4)
+SEARCH_CTAS_PER_SM = (0, 2, 4, 8)  # 0: one CTA per tile
 
 
 def signature(block, systems, nodes, precision, sms):
@@ -46,8 +45,7 @@ def _store(cache):
 def candidates():
     for th in SEARCH_THREADS:
         for c in SEARCH_CTAS_PER_SM:
-            for m in SEARCH_TILE_MULT:
-                yield fnlh.fnlh_tuning(th, c, th * m, 0)
+            yield fnlh.fnlh_tuning(th, c)
 
 
 def tune_batched(time_ms, key=None, use_cache=True):
@@ -55,17 +53,15 @@ def tune_batched(time_ms, key=None, use_cache=True):
     cache = _load() if (use_cache and key) else {}
     if key and key in cache:
         t = cache[key]
-        return fnlh.fnlh_tuning(t["threads"], t["ctas_per_sm"], t["tile_pairs"], 0), cache[key].get("table", [])
+        return fnlh.fnlh_tuning(t["threads"], t["ctas_per_sm"]), cache[key].get("table", [])
     table = []
     best, best_ms = None, float("inf")
     for tn in candidates():
         ms = float(time_ms(tn))
-        table.append({"threads": tn.threads, "ctas_per_sm": tn.ctas_per_sm, "tile_pairs": tn.nodes_per_tile,
-                      "ms": ms})
+        table.append({"threads": tn.threads, "ctas_per_sm": tn.ctas_per_sm, "ms": ms})
         if ms < best_ms:
             best, best_ms = tn, ms
     if key:
-        cache[key] = {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm, "tile_pairs": best.nodes_per_tile,
-                      "ms": best_ms, "table": table}
+        cache[key] = {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm, "ms": best_ms, "table": table}
         _store(cache)
     return best, table

@@ -15,9 +15,9 @@ int prepare_impl(const fnlh_mesh*, fnlh_jacobian*, cudaStream_t);
 int relax_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, double*, int, int, void*,
                cudaStream_t);
 int solve_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, double*, int, double, int,
-               int, void*, int*, int*, double*, cudaStream_t);
+               int, int, void*, int*, int*, double*, cudaStream_t);
 int residual_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*, double*,
-                    float*, const double*, double*, void*, cudaStream_t);
+                    float*, const float*, int, double*, void*, cudaStream_t);
 Systems make_systems(int n_harm, const double* omega);
 int batched_impl(const fnlh_row*, int, int, int, const fnlh_tuning*, void*, size_t, cudaStream_t);
 size_t batched_extra_bytes(int n_rows);
@@ -154,9 +154,10 @@ size_t fnlh_prep_bytes(int32_t n_nodes, int32_t nnz, int32_t block, int32_t prep
   return prep_layout(n_nodes, nnz, block, prep_flags).total;
 }
 
-size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm) {
+size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision) {
   if (n_nodes < 0 || (block != 5 && block != 6) || n_harm < 0 || n_harm > FNLH_MAX_HARMONICS) return 0;
-  return ws_layout(n_nodes, block, n_harm, FNLH_F64).total;  // the FP64 layout is the largest
+  if (!valid_precision(precision)) return 0;
+  return ws_layout(n_nodes, block, n_harm, precision).total;
 }
 
 int fnlh_build_jacobian(const fnlh_mesh* mesh, const double* Q, const fnlh_params* params, fnlh_jacobian* J,
@@ -212,23 +213,24 @@ int fnlh_residual(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm,
   const WsLayout W = ws_layout(mesh->n_nodes, J->block, n_harm, FNLH_F64);
   if (workspace_bytes < W.vec[0]) return FNLH_ERR_WORKSPACE;  // partials only
   const Systems sys = make_systems(n_harm, omega);
-  return residual_launch(mesh, J, sys, B, X, r, nullptr, nullptr, norms, workspace, (cudaStream_t)stream);
+  return residual_launch(mesh, J, sys, B, X, r, nullptr, nullptr, 0, norms, workspace, (cudaStream_t)stream);
 }
 
 int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega, const double* B,
-               double* X, int32_t precision, double tol, int32_t inner_sweeps, int32_t max_checks, void* workspace,
-               size_t workspace_bytes, int32_t* checks_done, int32_t* sweeps_done, double* rel_res,
+               double* X, int32_t precision, double tol, int32_t inner_sweeps, int32_t max_checks, int32_t flags,
+               void* workspace, size_t workspace_bytes, int32_t* checks_done, int32_t* sweeps_done, double* rel_res,
                fnlh_stream_t stream) {
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || !(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
+  if (flags & ~FNLH_SOLVE_ZERO_GUESS) return FNLH_ERR_ARG;
   FNLH_TRY(check_systems(n_harm, omega));
   FNLH_TRY(check_prep(J, precision));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
-  return solve_impl(mesh, J, n_harm, omega, B, X, precision, tol, inner_sweeps, max_checks, workspace, checks_done,
-                    sweeps_done, rel_res, (cudaStream_t)stream);
+  return solve_impl(mesh, J, n_harm, omega, B, X, precision, tol, inner_sweeps, max_checks, flags, workspace,
+                    checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
 }
 
 size_t fnlh_batched_extra_bytes(int32_t n_rows) { return n_rows > 0 ? batched_extra_bytes(n_rows) : 0; }

@@ -220,9 +220,10 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
 // rot   [n][b][b] f64   Q_i
 // hess  [n][b][b] f64   Q_i^T (J_ii + D_i I) Q_i  (upper Hessenberg, zeros below)
 // hessf [n][b][b] f32   (when an F32/BF16 copy is requested)
+// rotf  [n][b][b] f32   Q_i in FP32 (same condition: the mixed solve's rotations)
 // offd64 / offd32 / offd16 [nnz][b][b] rotated off-diagonal copies
 struct PrepLayout {
-  size_t rot, hess, hessf, offd64, offd32, offd16, total;
+  size_t rot, hess, hessf, rotf, offd64, offd32, offd16, total;
 };
 
 inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) {
@@ -233,9 +234,11 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
   off = align256(off + (size_t)n * bb * 8);
   p.hess = off;
   off = align256(off + (size_t)n * bb * 8);
-  p.hessf = p.offd64 = p.offd32 = p.offd16 = (size_t)-1;
+  p.hessf = p.rotf = p.offd64 = p.offd32 = p.offd16 = (size_t)-1;
   if (flags & (FNLH_PREP_F32 | FNLH_PREP_BF16)) {
     p.hessf = off;
+    off = align256(off + (size_t)n * bb * 4);
+    p.rotf = off;
     off = align256(off + (size_t)n * bb * 4);
   }
   if (flags & FNLH_PREP_F64) {

@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
 template <int BS>
 __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* __restrict__ diag,
                                                        const double* __restrict__ D, double* __restrict__ rot,
-                                                       double* __restrict__ hess, float* __restrict__ hessf) {
+                                                       double* __restrict__ hess, float* __restrict__ hessf,
+                                                       float* __restrict__ rotf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double P[BS][BS], Q[BS][BS];
@@ -221,7 +222,9 @@ __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* 
   for (int r = 0; r < BS; ++r)
     for (int c = 0; c < BS; ++c) {
       const double h = tri ? ((r > c) ? 0.0 : T[r][c]) : ((r > c + 1) ? 0.0 : P[r][c]);
-      rot[(size_t)i * BS * BS + r * BS + c] = tri ? Z[r][c] : Q[r][c];
+      const double z = tri ? Z[r][c] : Q[r][c];
+      rot[(size_t)i * BS * BS + r * BS + c] = z;
+      if (rotf) rotf[(size_t)i * BS * BS + r * BS + c] = (float)z;
       hess[(size_t)i * BS * BS + r * BS + c] = h;
       if (hessf) hessf[(size_t)i * BS * BS + r * BS + c] = (float)h;
     }
@@ -286,9 +289,10 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   double* rot = at<double>(J->prep, L.rot);
   double* hess = at<double>(J->prep, L.hess);
   float* hessf = (L.hessf != (size_t)-1) ? at<float>(J->prep, L.hessf) : nullptr;
+  float* rotf = (L.rotf != (size_t)-1) ? at<float>(J->prep, L.rotf) : nullptr;
   const int n = J->n_nodes;
   if (n > 0) {
-    k_prepare_basis<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf);
+    k_prepare_basis<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf, rotf);
     FNLH_LAUNCH_CHECK();
   }
   double* o64 = (L.offd64 != (size_t)-1) ? at<double>(J->prep, L.offd64) : nullptr;

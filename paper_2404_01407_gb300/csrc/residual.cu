@@ -28,8 +28,9 @@ struct ResArgs {
   const double* B;
   const double* X;
   double* r;        // nullable [n][C][b]
-  float* r32rot;    // nullable [n][K][b] complex: Q_i^T r_i rounded to FP32
-  const double* rot;
+  float* r32rot;    // nullable [n][K][b] complex: Q_i^T r_i in FP32 (r rounded to FP32 first)
+  const float* rotf;  // Q_i in FP32 (with r32rot)
+  int32_t x_zero;     // x is zero: r = B without reading X
   double* partials; // [gridDim][2K]
   Systems sys;
 };
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
         rr[t] = br[t];
         ri[t] = bi[t];
       }
-      const int p0 = a.row_ptr[i], p1 = a.row_ptr[i + 1];
+      const int p0 = a.row_ptr[i], p1 = a.x_zero ? p0 : a.row_ptr[i + 1];
       for (int p = p0; p < p1; ++p) {
         const int j = a.col_idx[p];
         const double* xj = a.X + ((size_t)j * C + c0) * BS;
@@ -87,8 +88,8 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
       double xr[BS], xi[BS];
 #pragma unroll
       for (int t = 0; t < BS; ++t) {
-        xr[t] = xp[t];
-        xi[t] = cplx ? xp[BS + t] : 0.0;
+        xr[t] = a.x_zero ? 0.0 : xp[t];
+        xi[t] = (cplx && !a.x_zero) ? xp[BS + t] : 0.0;
       }
       const double* P = a.diag + (size_t)i * BS * BS;
       const double Di = a.D[i];
@@ -120,21 +121,28 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
         }
       }
       if (a.r32rot) {
-        // Q_i^T r in the sweeps' internal layout [n][K][b] complex (the mean
-        // flow's imaginary part is written as an exact zero)
-        const double* Q = a.rot + (size_t)i * BS * BS;
+        // Q_i^T r in the sweeps' internal layout [n][K][b] complex, in FP32:
+        // the inner solve only needs r to FP32 accuracy (the mean flow's
+        // imaginary part is written as an exact zero)
+        const float* Q = a.rotf + (size_t)i * BS * BS;
+        float fr[BS], fi[BS];
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+          fr[t] = (float)rr[t];
+          fi[t] = (float)ri[t];
+        }
         float* rp = a.r32rot + ((size_t)i * K + k) * 2 * BS;
 #pragma unroll
         for (int q = 0; q < BS; ++q) {
-          double ar = 0.0, ai = 0.0;
+          float ar = 0.0f, ai = 0.0f;
 #pragma unroll
           for (int t = 0; t < BS; ++t) {
-            const double qv = __ldg(Q + t * BS + q);
-            ar += qv * rr[t];
-            ai += qv * ri[t];
+            const float qv = __ldg(Q + t * BS + q);
+            ar += qv * fr[t];
+            ai += qv * fi[t];
           }
-          rp[2 * q] = (float)ar;
-          rp[2 * q + 1] = cplx ? (float)ai : 0.0f;
+          rp[2 * q] = ar;
+          rp[2 * q + 1] = cplx ? ai : 0.0f;
         }
       }
     }
@@ -163,7 +171,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nblk,
 }
 
 int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
-                    const double* X, double* r, float* r32rot, const double* rot, double* norms, void* ws,
+                    const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
                     cudaStream_t s) {
   const WsLayout W = ws_layout(J->n_nodes, J->block, sys.K - 1, FNLH_F64);
   ResArgs a;
@@ -178,7 +186,8 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   a.X = X;
   a.r = r;
   a.r32rot = r32rot;
-  a.rot = rot;
+  a.rotf = rotf;
+  a.x_zero = x_zero;
   a.partials = at<double>(ws, W.partials);
   a.sys = sys;
   const long long total = (long long)a.n * sys.K;
@@ -249,7 +258,8 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   a.X = X;
   a.r = r;
   a.r32rot = nullptr;
-  a.rot = nullptr;
+  a.rotf = nullptr;
+  a.x_zero = 0;
   a.partials = partials;
   a.sys = sys;
   if (J->block == 5) k_residual<5><<<grid, kResidualThreads, 0, s>>>(a);

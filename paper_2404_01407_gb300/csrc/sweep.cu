@@ -27,6 +27,8 @@ constexpr int kSweepThreads = 256;
 
 struct SweepArgs {
   TileRow row;
+  const void* Xin;
+  void* Xout;
   int32_t x_zero;
   int32_t smem_floats;
   int32_t* status;  // workspace status word (bit 0: a bounded wait timed out)
@@ -38,18 +40,16 @@ template <int BS>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)a.row.n * a.row.K) return;
-  TileRow R = a.row;
-  R.omega = a.omega;
-  sweep_pair_f64<BS>(R, g, a.x_zero != 0);
+  const SweepIO io{a.Xin, a.Xout, a.omega};
+  sweep_pair_f64<BS>(a.row, io, g, a.x_zero != 0);
 }
 
 // FP32 arithmetic on FP32 or BF16 blocks, staged per CTA tile.
 template <int BS, typename TJ>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_f32(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(16) float smem[];
-  TileRow R = a.row;
-  R.omega = a.omega;
-  sweep_tile_f32<BS, TJ>(R, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
+  const SweepIO io{a.Xin, a.Xout, a.omega};
+  sweep_tile_f32<BS, TJ>(a.row, io, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
 }
 
 // Caller layout [n][C][b] (FP64) -> internal [n][K][b] complex, y = Q_i^T x,
@@ -118,6 +118,39 @@ __global__ void __launch_bounds__(256) k_rotate_out(long long count, int K, cons
   }
 }
 
+// x_i[c] += Q_i y_i[c] with the product in FP32 and the sum in FP64: the
+// defect-correction update, whose correction only needs FP32 accuracy.
+template <int BS>
+__global__ void __launch_bounds__(256) k_update_f32(long long count, int K, const float* __restrict__ rotf,
+                                                    const float* __restrict__ y, double* __restrict__ x) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  const long long i = g / K;
+  const int k = (int)(g - i * K);
+  const int C = 2 * K - 1;
+  const float* Q = rotf + i * BS * BS;
+  const float* in = y + g * 2 * BS;
+  float vr[BS], vi[BS];
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    vr[t] = in[2 * t];
+    vi[t] = in[2 * t + 1];
+  }
+  double* xr = x + (i * C + (k == 0 ? 0 : 2 * k - 1)) * BS;
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    float ar = 0.0f, ai = 0.0f;
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      const float q = __ldg(Q + r * BS + t);
+      ar += q * vr[t];
+      ai += q * vi[t];
+    }
+    xr[r] += (double)ar;
+    if (k > 0) xr[BS + r] += (double)ai;
+  }
+}
+
 static inline unsigned blocks_for(long long count, int threads) {
   return (unsigned)((count + threads - 1) / threads);
 }
@@ -145,11 +178,13 @@ struct SweepOperands {
   const void* offd;
   const void* hess;
   const double* rot;
+  const float* rotf;  // FP32 basis (low-precision sweeps only)
 };
 
 int sweep_operands(const fnlh_jacobian* J, int precision, SweepOperands* o) {
   const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
   o->rot = at<double>(J->prep, L.rot);
+  o->rotf = (L.rotf != (size_t)-1) ? at<float>(J->prep, L.rotf) : nullptr;
   if (precision == FNLH_F64) {
     if (L.offd64 == (size_t)-1) return FNLH_ERR_WORKSPACE;
     o->offd = at<double>(J->prep, L.offd64);
@@ -240,8 +275,8 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   T* nxt = x1;
   if ((rc = mark(g_ev_begin, s))) return rc;
   for (int it = 0; it < sweeps; ++it) {
-    a.row.Xin = cur;
-    a.row.Xout = nxt;
+    a.Xin = cur;
+    a.Xout = nxt;
     a.x_zero = (it == 0) ? x_zero : 0;
     if ((rc = sweep_launch<BS, TJ, T>(a, smem, s))) return rc;
     T* t = cur;
@@ -287,7 +322,7 @@ int relax_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const dou
 // ------------------------------------------------------------------ solve
 
 int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
-                    const double* X, double* r, float* r32rot, const double* rot, double* norms, void* ws,
+                    const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
                     cudaStream_t s);
 
 struct Check {
@@ -314,8 +349,8 @@ static int check_norms(const double* hn, int K, double tol, Check* ck, bool firs
 
 template <int BS, typename TJ, typename T>
 int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-                double* X, int precision, double tol, int inner, int max_checks, void* ws, int* checks_done,
-                int* sweeps_done, double* rel_res, cudaStream_t s) {
+                double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
+                int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
   SweepOperands op;
   int rc = sweep_operands(J, precision, &op);
   if (rc) return rc;
@@ -332,6 +367,8 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   int checks = 0, sweeps = 0;
   bool conv = false;
   const bool mixed = precision != FNLH_F64;
+  bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
+  if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
   if (!mixed) {
     // plain FP64 Jacobi: iterate in the rotated basis, check every `inner` sweeps
     if ((rc = rotate_in<BS, T>(n, K, op.rot, B, v0, s))) return rc;
@@ -340,7 +377,9 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   T* cur = v1;
   FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   for (;;) {
-    rc = residual_launch(m, J, sys, B, X, nullptr, mixed ? (float*)v0 : nullptr, op.rot, norms, ws, s);
+    rc = residual_launch(m, J, sys, B, X, nullptr, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms,
+                         ws, s);
+    x_zero = false;
     if (rc) return rc;
     int32_t hstatus = 0;
     FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
@@ -357,7 +396,11 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     if (mixed) {
       // inner: A~ e = r~ from e = 0 (v1/v2 ping-pong), then x += Q e in FP64
       if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res))) return rc;
-      if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 1, s))) return rc;
+      const long long count = (long long)n * K;
+      if (count > 0) {
+        k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X);
+        FNLH_LAUNCH_CHECK();
+      }
     } else {
       T* other = (cur == v1) ? v2 : v1;
       if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res))) return rc;
@@ -375,10 +418,11 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
 }
 
 int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-               double* X, int precision, double tol, int inner, int max_checks, void* ws, int* checks_done,
-               int* sweeps_done, double* rel_res, cudaStream_t s) {
-#define FNLH_SOLVE(BS, TJ, T) \
-  solve_typed<BS, TJ, T>(m, J, n_harm, omega, B, X, precision, tol, inner, max_checks, ws, checks_done, sweeps_done, rel_res, s)
+               double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
+               int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
+#define FNLH_SOLVE(BS, TJ, T)                                                                                  \
+  solve_typed<BS, TJ, T>(m, J, n_harm, omega, B, X, precision, tol, inner, max_checks, flags, ws, checks_done, \
+                         sweeps_done, rel_res, s)
   if (J->block == 5) {
     if (precision == FNLH_F64) return FNLH_SOLVE(5, double, double);
     if (precision == FNLH_F32) return FNLH_SOLVE(5, float, float);
@@ -392,11 +436,12 @@ int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const dou
 
 // ----------------------------------------------------------- batched rows
 //
-// Several blade rows (different meshes and harmonic counts) in one
-// persistent launch per sweep.  The (node, system) pairs of every row are cut
-// into tiles of blockDim.x consecutive pairs; a grid of SMs x ctas_per_sm
-// CTAs walks the global tile list round-robin, so the rows share one launch
-// and one tail instead of each paying its own.  The row descriptors travel as
+// Several blade rows (different meshes and harmonic counts) in one launch per
+// sweep.  The (node, system) pairs of every row are cut into tiles of
+// blockDim.x consecutive pairs; the grid walks the global tile list -- one
+// CTA per tile, or a persistent grid of SMs x ctas_per_sm CTAs striding over
+// it -- so the rows share one launch and one tail instead of each paying its
+// own.  The row descriptors travel as
 // a __grid_constant__ kernel parameter (no device memory, capturable in a
 // CUDA graph).
 
@@ -421,16 +466,14 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched(const __grid
   for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
     int r = 0;
     while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
-    TileRow R = a.row[r].row;
-    R.omega = a.row[r].omega;
-    R.Xin = a.row[r].x[a.parity];
-    R.Xout = a.row[r].x[a.parity ^ 1];
-    const long long g0 = (t - a.row[r].tile0) * blockDim.x;
+    const BatchRow& D = a.row[r];
+    const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega};
+    const long long g0 = (t - D.tile0) * blockDim.x;
     if constexpr (sizeof(T) == 8) {
       const long long g = g0 + threadIdx.x;
-      if (g < (long long)R.n * R.K) sweep_pair_f64<BS>(R, g, false);
+      if (g < (long long)D.row.n * D.row.K) sweep_pair_f64<BS>(D.row, io, g, false);
     } else {
-      sweep_tile_f32<BS, TJ>(R, g0, false, smem, a.smem_floats);
+      sweep_tile_f32<BS, TJ>(D.row, io, g0, false, smem, a.smem_floats);
     }
   }
 }
@@ -443,7 +486,7 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   static thread_local BatchArgs a;  // large: kept off the stack (the launch copies it)
   std::memset(&a, 0, sizeof(a));
   const int threads = (tn && tn->threads > 0) ? tn->threads : kSweepThreads;
-  const int ctas_per_sm = (tn && tn->ctas_per_sm > 0) ? tn->ctas_per_sm : 4;
+  const int ctas_per_sm = tn ? tn->ctas_per_sm : 0;  // 0: one CTA per tile
   if (threads > kSweepThreads || threads % 32) return FNLH_ERR_ARG;
   int dev = 0, sms = 0;
   FNLH_CUDA_TRY(cudaGetDevice(&dev));
@@ -483,10 +526,12 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   a.n_tiles = tiles;
   size_t smem = 0;
   if constexpr (sizeof(T) == 4) {
+    // sized for the row with the fewest systems (the largest stage; two CTAs
+    // per SM still fit), so that every row's tiles are staged
     int rc = stage_setup(k_sweep_batched<BS, TJ, T>, threads, kmin, BS, &a.smem_floats, &smem);
     if (rc) return rc;
   }
-  const long long grid_ll = std::min<long long>(tiles, (long long)sms * ctas_per_sm);
+  const long long grid_ll = (ctas_per_sm > 0) ? std::min<long long>(tiles, (long long)sms * ctas_per_sm) : tiles;
   const unsigned grid = (unsigned)std::max<long long>(grid_ll, 1);
   {
     int rc = mark(g_ev_begin, s);

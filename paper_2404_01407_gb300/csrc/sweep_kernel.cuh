@@ -231,28 +231,34 @@ struct TileRow {
   const void* hess;  // [n][b][b] (double for FP64 sweeps, float otherwise)
   const double* vol;
   const void* Bt;    // [n][K][b] complex, right-hand side in the rotated basis
-  const void* Xin;   // [n][K][b] complex (not read when x_zero)
-  void* Xout;
-  const double* omega;  // [K], omega[0] = 0
+};
+
+// The iterate buffers and frequencies of one launch (the row descriptor
+// itself is read in place from the kernel parameters).
+struct SweepIO {
+  const void* Xin;       // [n][K][b] complex (not read when x_zero)
+  void* Xout;            // [n][K][b] complex
+  const double* omega;   // [K], omega[0] = 0
 };
 
 // Shifted Hessenberg solve + store for one pair, shared by both forms.
 template <int BS, typename T, typename TH>
-__device__ __forceinline__ void finish_pair(const TileRow& R, const TH* H, int i, int k, Cvec<BS, T>& s) {
-  const T shift = (T)(R.omega[k] * __ldg(R.vol + i));
+__device__ __forceinline__ void finish_pair(const TileRow& R, const SweepIO& io, const TH* H, int i, int k,
+                                            Cvec<BS, T>& s) {
+  const T shift = (T)(io.omega[k] * __ldg(R.vol + i));
   hess_solve<BS, T>(H, shift, s.re, s.im);
-  store_slice<BS>((T*)R.Xout + ((size_t)i * R.K + k) * 2 * BS, s);
+  store_slice<BS>((T*)io.Xout + ((size_t)i * R.K + k) * 2 * BS, s);
 }
 
 // FP64 (or unstaged) form: blocks and factors straight from global memory.
 template <int BS>
-__device__ __forceinline__ void sweep_pair_f64(const TileRow& R, long long g, bool x_zero) {
+__device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& io, long long g, bool x_zero) {
   const int i = (int)fdiv((uint32_t)g, R.divK);
   const int k = (int)g - i * R.K;
   Cvec<BS, double> s;
   load_slice<BS>((const double*)R.Bt + ((size_t)i * R.K + k) * 2 * BS, s);
   if (!x_zero) {
-    const double* __restrict__ X = (const double*)R.Xin;
+    const double* __restrict__ X = (const double*)io.Xin;
     const double* __restrict__ offd = (const double*)R.offd;
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
@@ -270,15 +276,15 @@ __device__ __forceinline__ void sweep_pair_f64(const TileRow& R, long long g, bo
         }
     }
   }
-  finish_pair<BS, double>(R, (const double*)R.hess + (size_t)i * BS * BS, i, k, s);
+  finish_pair<BS, double>(R, io, (const double*)R.hess + (size_t)i * BS * BS, i, k, s);
 }
 
 // Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
 // Every thread of the CTA must call it (it synchronises).
 // Every thread of the CTA must call this (it synchronises).
 template <int BS, typename TJ>
-__device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, bool x_zero, float* smem,
-                                               int smem_floats) {
+__device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& io, long long g0, bool x_zero,
+                                               float* smem, int smem_floats) {
   const uint32_t total = (uint32_t)R.n * (uint32_t)R.K;
   const uint32_t gs = (uint32_t)g0;
   const uint32_t g = gs + threadIdx.x;
@@ -312,7 +318,7 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, b
     const int i = (int)fdiv(g, R.divK);
     const int k = (int)g - i * R.K;
     if (!x_zero) {
-      const float* __restrict__ Xk = (const float*)R.Xin + (size_t)k * 2 * BS;
+      const float* __restrict__ Xk = (const float*)io.Xin + (size_t)k * 2 * BS;
       const size_t stride = (size_t)R.K * 2 * BS;
       const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
       // software pipeline: the next neighbour's slice is in flight while the
@@ -350,7 +356,7 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, long long g0, b
       }
     }
     const float* H = staged ? sH + (size_t)(i - i_first) * BS * BS : (const float*)R.hess + (size_t)i * BS * BS;
-    finish_pair<BS, float>(R, H, i, k, s);
+    finish_pair<BS, float>(R, io, H, i, k, s);
   }
   __syncthreads();  // the stage buffer is reused by the next tile
 }

@@ -64,7 +64,7 @@ class fnlh_row(ctypes.Structure):
 
 
 class fnlh_tuning(ctypes.Structure):
-    _fields_ = [("threads", c_i32), ("ctas_per_sm", c_i32), ("nodes_per_tile", c_i32), ("reserved", c_i32)]
+    _fields_ = [("threads", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32 * 2)]
 
 
 class FnlhError(RuntimeError):
@@ -82,7 +82,7 @@ _SIGS = {
     "fnlh_version": (ctypes.c_int, []),
     "fnlh_mesh_build_csr": (ctypes.c_int, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "fnlh_prep_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
-    "fnlh_workspace_bytes": (c_sz, [c_i32, c_i32, c_i32]),
+    "fnlh_workspace_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
     "fnlh_build_jacobian": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), c_vp, ctypes.POINTER(fnlh_params),
                                            ctypes.POINTER(fnlh_jacobian), c_vp]),
     "fnlh_prepare": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_vp]),
@@ -91,7 +91,7 @@ _SIGS = {
     "fnlh_residual": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
                                      ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "fnlh_solve": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
-                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_f64, c_i32, c_i32, c_vp, c_sz,
+                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_f64, c_i32, c_i32, c_i32, c_vp, c_sz,
                                   ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_f64), c_vp]),
     "fnlh_relax_batched": (ctypes.c_int, [ctypes.POINTER(fnlh_row), c_i32, c_i32, c_i32,
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
@@ -210,8 +210,8 @@ def make_params(cfl, gamma=1.4, entropy_delta=0.1, pseudo_time=0, eps=0.6):
     return fnlh_params(gamma, cfl, entropy_delta, pseudo_time, eps)
 
 
-def workspace(n_nodes, block, n_harm, device="cuda"):
-    nbytes = fnlh_workspace_bytes(n_nodes, block, n_harm)
+def workspace(n_nodes, block, n_harm, device="cuda", precision=FNLH_F64):
+    nbytes = fnlh_workspace_bytes(n_nodes, block, n_harm, precision)
     return torch.empty((nbytes,), dtype=torch.uint8, device=device)
 
 
@@ -236,8 +236,8 @@ def fnlh_prep_bytes(n_nodes, nnz, block, prep_flags) -> int:
     return int(lib().fnlh_prep_bytes(n_nodes, nnz, block, prep_flags))
 
 
-def fnlh_workspace_bytes(n_nodes, block, n_harm) -> int:
-    return int(lib().fnlh_workspace_bytes(n_nodes, block, n_harm))
+def fnlh_workspace_bytes(n_nodes, block, n_harm, precision=FNLH_F64) -> int:
+    return int(lib().fnlh_workspace_bytes(n_nodes, block, n_harm, precision))
 
 
 def fnlh_build_jacobian(dmesh: DeviceMesh, Q: torch.Tensor, params: fnlh_params, J: DeviceJacobian, stream=None):
@@ -275,8 +275,11 @@ def fnlh_residual(dmesh, J, omega, B, X, r=None, norms=None, ws=None, stream=Non
     return norms
 
 
+FNLH_SOLVE_ZERO_GUESS = 1
+
+
 def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, ws=None, stream=None,
-               raise_on_error=True):
+               raise_on_error=True, flags=0):
     """Returns (status, checks_done, sweeps_done, rel_res[K])."""
     om, omp = _omega(omega)
     n_harm = len(np.atleast_1d(omega))
@@ -285,7 +288,8 @@ def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, 
     checks, sweeps = c_i32(0), c_i32(0)
     rel = (c_f64 * (1 + n_harm))()
     st = lib().fnlh_solve(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), int(precision),
-                          float(tol), int(inner_sweeps), int(max_checks), _ptr(ws), ws.numel(), ctypes.byref(checks),
+                          float(tol), int(inner_sweeps), int(max_checks), int(flags), _ptr(ws), ws.numel(),
+                          ctypes.byref(checks),
                           ctypes.byref(sweeps), rel, _stream(stream))
     if raise_on_error and st != FNLH_OK:
         raise FnlhError(st, "fnlh_solve")

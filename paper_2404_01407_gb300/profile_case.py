@@ -50,8 +50,7 @@ def main():
         elif a.op == "build":
             fnlh.fnlh_build_jacobian(dm, Q, params, J)
         else:
-            X.zero_()
-            fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, a.sweeps, 50, ws=ws)
+            fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, a.sweeps, 50, ws=ws, flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
 
     for _ in range(a.warm):
         op()

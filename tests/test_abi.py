@@ -70,8 +70,11 @@ def test_sizes_independent_of_harmonics():
     assert prep > 0
     ws = [fnlh.fnlh_workspace_bytes(n, 6, N) for N in (0, 1, 16, 64)]
     assert ws[0] < ws[1] < ws[2] < ws[3]
+    assert fnlh.fnlh_workspace_bytes(n, 6, 16, fnlh.FNLH_F32) < ws[2]
+    assert fnlh.fnlh_workspace_bytes(n, 6, 16, fnlh.FNLH_BF16) == fnlh.fnlh_workspace_bytes(n, 6, 16, fnlh.FNLH_F32)
     assert fnlh.fnlh_workspace_bytes(n, 6, 65) == 0
     assert fnlh.fnlh_workspace_bytes(n, 7, 1) == 0
+    assert fnlh.fnlh_workspace_bytes(n, 6, 1, 9) == 0
     assert fnlh.fnlh_prep_bytes(n, nnz, 4, 1) == 0
 
 

@@ -127,12 +127,15 @@ def test_relax_low_precision_bounded(prec, bound):
 
 
 @pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
-def test_mixed_solve_reaches_1e8(prec):
-    """Defect correction: FP64 residual, low-precision inner sweeps, FP64 update."""
+@pytest.mark.parametrize("zero_guess", [False, True])
+def test_mixed_solve_reaches_1e8(prec, zero_guess):
+    """Defect correction: FP64 residual, low-precision inner sweeps, FP64 update.
+    With FNLH_SOLVE_ZERO_GUESS the incoming X (garbage here) is ignored."""
     p = inputs.problem((32, 24, 16), 6, 8, 20.0, name="c3_reduced")
     dm, J, B = _gpu.device_problem(p)
-    X = torch.zeros_like(B)
-    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40)
+    X = torch.full_like(B, 1e30) if zero_guess else torch.zeros_like(B)
+    flags = fnlh.FNLH_SOLVE_ZERO_GUESS if zero_guess else 0
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40, flags=flags)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     oj = _gpu.oracle_jacobian(p)
     x = X.cpu().numpy()
@@ -143,11 +146,13 @@ def test_mixed_solve_reaches_1e8(prec):
     assert np.all(err <= 1e-6), err
 
 
-def test_plain_f64_solve_matches_oracle():
+@pytest.mark.parametrize("zero_guess", [False, True])
+def test_plain_f64_solve_matches_oracle(zero_guess):
     p = small("b6n4")
     dm, J, B = _gpu.device_problem(p)
-    X = torch.zeros_like(B)
-    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-10, 10, 100)
+    X = torch.full_like(B, -3.0) if zero_guess else torch.zeros_like(B)
+    flags = fnlh.FNLH_SOLVE_ZERO_GUESS if zero_guess else 0
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-10, 10, 100, flags=flags)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-10)
     oj = _gpu.oracle_jacobian(p)
     ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, sweeps)
@@ -171,7 +176,7 @@ def test_batched_rows_match_per_row():
     Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
     batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
     ws = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
-    for tn in (None, fnlh.fnlh_tuning(128, 2, 96, 0)):
+    for tn in (None, fnlh.fnlh_tuning(128, 2), fnlh.fnlh_tuning(256, 0)):
         for X in Xs:
             X.zero_()
         fnlh.fnlh_relax_batched(batch, 13, fnlh.FNLH_F32, tuning=tn, ws=ws)
