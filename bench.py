@@ -39,9 +39,10 @@ WORKLOAD = "c2"
 
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM bytes per launch of the top kernel from the last ncu capture of the
-# kernel as it stands (None until captured for this version of the kernel)
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the top kernel from the last ncu
+# capture of the kernel as it stands on this workload (profiles/k_sweep_f64_c2.md);
+# to be reset to None whenever the kernel changes
+NCU_TRAFFIC = {"k_sweep_f64_c2": 1.174262e9 + 0.177406e9}
 
 
 def tri_solve_flops(b: int, real: bool) -> int:
