@@ -6,11 +6,12 @@
 // always formed in FP64 from the FP64 blocks in the original basis, which is
 // what lets the mixed-precision sweeps be corrected back to FP64 accuracy.
 //
-// Determinism: a fixed grid walks the (node, system) pairs in a fixed
-// pattern; every block reduces its pairs per system in index order through
-// shared memory, and one final pass sums the block partials in block order.
+// Determinism: a fixed grid walks tiles of 32 nodes in a fixed pattern; each
+// block accumulates per-system sums in tile order through fixed shuffle
+// trees, and one final pass sums the block partials in block order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -35,64 +36,69 @@ struct ResArgs {
   Systems sys;
 };
 
+// r for one (node, system) pair; returns ||r||^2 and ||B||^2 contributions.
+// The mean flow (k = 0) takes a real-only path.
 template <int BS>
-__global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
-  __shared__ int s_k[kResidualThreads];
-  __shared__ double s_r[kResidualThreads], s_b[kResidualThreads];
-  const int K = a.sys.K, C = a.sys.C;
-  const long long total = (long long)a.n * K;
-  // per-block accumulators: thread t < 2K owns (system t/2, r or b)
-  double acc = 0.0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-    const long long g = base + threadIdx.x;
-    double rs = 0.0, bs = 0.0;
-    int kk = -1;
-    if (g < total) {
-      const int i = (int)(g / K);
-      const int k = (int)(g - (long long)i * K);
-      kk = k;
-      const int c0 = (k == 0) ? 0 : 2 * k - 1;
-      const bool cplx = k > 0;
-      double br[BS], bi[BS], rr[BS], ri[BS];
-      const double* bp = a.B + ((size_t)i * C + c0) * BS;
+__device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, double& rs, double& bs) {
+  const int C = a.sys.C;
+  const int c0 = (k == 0) ? 0 : 2 * k - 1;
+  const bool cplx = k > 0;
+  double br[BS], bi[BS], rr[BS], ri[BS];
+  const double* bp = a.B + ((size_t)i * C + c0) * BS;
 #pragma unroll
-      for (int t = 0; t < BS; ++t) {
-        br[t] = bp[t];
-        bi[t] = cplx ? bp[BS + t] : 0.0;
-        rr[t] = br[t];
-        ri[t] = bi[t];
-      }
-      const int p0 = a.row_ptr[i], p1 = a.x_zero ? p0 : a.row_ptr[i + 1];
-      for (int p = p0; p < p1; ++p) {
-        const int j = a.col_idx[p];
-        const double* xj = a.X + ((size_t)j * C + c0) * BS;
-        double xr[BS], xi[BS];
-#pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          xr[t] = __ldg(xj + t);
-          xi[t] = cplx ? __ldg(xj + BS + t) : 0.0;
-        }
-        const double* J = a.offd + (size_t)p * BS * BS;
-#pragma unroll
-        for (int q = 0; q < BS; ++q)
-#pragma unroll
-          for (int t = 0; t < BS; ++t) {
-            const double jv = __ldg(J + q * BS + t);
-            rr[q] -= jv * xr[t];
-            ri[q] -= jv * xi[t];
-          }
-      }
-      // diagonal block, D and the spectral term i omega V
-      const double* xp = a.X + ((size_t)i * C + c0) * BS;
+  for (int t = 0; t < BS; ++t) {
+    br[t] = bp[t];
+    bi[t] = cplx ? bp[BS + t] : 0.0;
+    rr[t] = br[t];
+    ri[t] = bi[t];
+  }
+  const int p0 = a.row_ptr[i], p1 = a.x_zero ? p0 : a.row_ptr[i + 1];
+  if (cplx) {
+    for (int p = p0; p < p1; ++p) {
+      const int j = a.col_idx[p];
+      const double* xj = a.X + ((size_t)j * C + c0) * BS;
       double xr[BS], xi[BS];
 #pragma unroll
       for (int t = 0; t < BS; ++t) {
-        xr[t] = a.x_zero ? 0.0 : xp[t];
-        xi[t] = (cplx && !a.x_zero) ? xp[BS + t] : 0.0;
+        xr[t] = __ldg(xj + t);
+        xi[t] = __ldg(xj + BS + t);
       }
-      const double* P = a.diag + (size_t)i * BS * BS;
-      const double Di = a.D[i];
+      const double* J = a.offd + (size_t)p * BS * BS;
+#pragma unroll
+      for (int q = 0; q < BS; ++q)
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+          const double jv = __ldg(J + q * BS + t);
+          rr[q] -= jv * xr[t];
+          ri[q] -= jv * xi[t];
+        }
+    }
+  } else {
+    for (int p = p0; p < p1; ++p) {
+      const int j = a.col_idx[p];
+      const double* xj = a.X + (size_t)j * C * BS;
+      double xr[BS];
+#pragma unroll
+      for (int t = 0; t < BS; ++t) xr[t] = __ldg(xj + t);
+      const double* J = a.offd + (size_t)p * BS * BS;
+#pragma unroll
+      for (int q = 0; q < BS; ++q)
+#pragma unroll
+        for (int t = 0; t < BS; ++t) rr[q] -= __ldg(J + q * BS + t) * xr[t];
+    }
+  }
+  // diagonal block, D and the spectral term i omega V
+  if (!a.x_zero) {
+    const double* xp = a.X + ((size_t)i * C + c0) * BS;
+    double xr[BS], xi[BS];
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      xr[t] = xp[t];
+      xi[t] = cplx ? xp[BS + t] : 0.0;
+    }
+    const double* P = a.diag + (size_t)i * BS * BS;
+    const double Di = a.D[i];
+    if (cplx) {
       const double wv = a.sys.omega[k] * a.vol[i];
 #pragma unroll
       for (int q = 0; q < BS; ++q) {
@@ -107,58 +113,87 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(ResArgs a) {
         rr[q] += wv * xi[q];
         ri[q] -= wv * xr[q];
       }
+    } else {
+#pragma unroll
+      for (int q = 0; q < BS; ++q) {
+#pragma unroll
+        for (int t = 0; t < BS; ++t) rr[q] -= __ldg(P + q * BS + t) * xr[t];
+        rr[q] -= Di * xr[q];
+      }
+    }
+  }
+  rs = 0.0;
+  bs = 0.0;
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    rs += rr[t] * rr[t] + ri[t] * ri[t];
+    bs += br[t] * br[t] + bi[t] * bi[t];
+  }
+  if (a.r) {
+    double* rp = a.r + ((size_t)i * C + c0) * BS;
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      rp[t] = rr[t];
+      if (cplx) rp[BS + t] = ri[t];
+    }
+  }
+  if (a.r32rot) {
+    // Q_i^T r in the sweeps' internal layout [n][K][b] complex, in FP32:
+    // the inner solve only needs r to FP32 accuracy (the mean flow's
+    // imaginary part is written as an exact zero)
+    const float* Q = a.rotf + (size_t)i * BS * BS;
+    float fr[BS], fi[BS];
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      fr[t] = (float)rr[t];
+      fi[t] = (float)ri[t];
+    }
+    float* rp = a.r32rot + ((size_t)i * a.sys.K + k) * 2 * BS;
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      float ar = 0.0f, ai = 0.0f;
 #pragma unroll
       for (int t = 0; t < BS; ++t) {
-        rs += rr[t] * rr[t] + ri[t] * ri[t];
-        bs += br[t] * br[t] + bi[t] * bi[t];
+        const float qv = __ldg(Q + t * BS + q);
+        ar += qv * fr[t];
+        ai += qv * fi[t];
       }
-      if (a.r) {
-        double* rp = a.r + ((size_t)i * C + c0) * BS;
-#pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          rp[t] = rr[t];
-          if (cplx) rp[BS + t] = ri[t];
-        }
-      }
-      if (a.r32rot) {
-        // Q_i^T r in the sweeps' internal layout [n][K][b] complex, in FP32:
-        // the inner solve only needs r to FP32 accuracy (the mean flow's
-        // imaginary part is written as an exact zero)
-        const float* Q = a.rotf + (size_t)i * BS * BS;
-        float fr[BS], fi[BS];
-#pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          fr[t] = (float)rr[t];
-          fi[t] = (float)ri[t];
-        }
-        float* rp = a.r32rot + ((size_t)i * K + k) * 2 * BS;
-#pragma unroll
-        for (int q = 0; q < BS; ++q) {
-          float ar = 0.0f, ai = 0.0f;
-#pragma unroll
-          for (int t = 0; t < BS; ++t) {
-            const float qv = __ldg(Q + t * BS + q);
-            ar += qv * fr[t];
-            ai += qv * fi[t];
-          }
-          rp[2 * q] = ar;
-          rp[2 * q + 1] = cplx ? ai : 0.0f;
-        }
-      }
+      rp[2 * q] = ar;
+      rp[2 * q + 1] = cplx ? ai : 0.0f;
     }
-    s_k[threadIdx.x] = kk;
-    s_r[threadIdx.x] = rs;
-    s_b[threadIdx.x] = bs;
-    __syncthreads();
-    if (threadIdx.x < 2 * K) {
-      const int mine = threadIdx.x >> 1;
-      const bool want_b = threadIdx.x & 1;
-      for (int t = 0; t < blockDim.x; ++t)
-        if (s_k[t] == mine) acc += want_b ? s_b[t] : s_r[t];
-    }
-    __syncthreads();
   }
-  if (threadIdx.x < 2 * K) a.partials[(size_t)blockIdx.x * 2 * K + threadIdx.x] = acc;
+}
+
+// One block walks tiles of 32 nodes (grid stride); within a tile each warp
+// takes whole systems (lane = node), reduces them with a fixed shuffle tree
+// and adds them, in tile order, to the block's per-system sums -- one writer
+// per system per tile, so the result is bit-reproducible.
+template <int BS>
+__global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_constant__ ResArgs a) {
+  __shared__ double s_acc[2 * kMaxSys];
+  const int K = a.sys.K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_acc[t] = 0.0;
+  __syncthreads();
+  const int tiles = (a.n + 31) / 32;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int i = tile * 32 + lane;
+    for (int k = warp; k < K; k += nwarps) {
+      double rs = 0.0, bs = 0.0;
+      if (i < a.n) residual_pair<BS>(a, i, k, rs, bs);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        rs += __shfl_xor_sync(0xffffffffu, rs, off);
+        bs += __shfl_xor_sync(0xffffffffu, bs, off);
+      }
+      if (lane == 0) {
+        s_acc[2 * k] += rs;
+        s_acc[2 * k + 1] += bs;
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) a.partials[(size_t)blockIdx.x * 2 * K + t] = s_acc[t];
 }
 
 // norms[t] = sum over blocks of partials[blk][t], in block order.
@@ -168,6 +203,12 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nblk,
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * width + t];
   norms[t] = s;
+}
+
+// Fixed grid (a function of n only), so that repeated calls sum in the same order.
+static int residual_grid(int n) {
+  const int tiles = (n + 31) / 32;
+  return tiles < 1 ? 1 : (tiles < kResidualGrid ? tiles : kResidualGrid);
 }
 
 int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
@@ -190,11 +231,10 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   a.x_zero = x_zero;
   a.partials = at<double>(ws, W.partials);
   a.sys = sys;
-  const long long total = (long long)a.n * sys.K;
-  long long need = (total + kResidualThreads - 1) / kResidualThreads;
-  const int grid = (int)(need < kResidualGrid ? (need > 0 ? need : 1) : kResidualGrid);
-  if (J->block == 5) k_residual<5><<<grid, kResidualThreads, 0, s>>>(a);
-  else k_residual<6><<<grid, kResidualThreads, 0, s>>>(a);
+  const int grid = residual_grid(a.n);
+  const int threads = 32 * std::min(sys.K, kResidualThreads / 32);
+  if (J->block == 5) k_residual<5><<<grid, threads, 0, s>>>(a);
+  else k_residual<6><<<grid, threads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
   k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(a.partials, grid, 2 * sys.K, norms);
   FNLH_LAUNCH_CHECK();
@@ -239,9 +279,7 @@ static int scratch_address(double** out) {
 
 int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
                             const double* X, double* r, double* norms, cudaStream_t s) {
-  const long long total = (long long)J->n_nodes * sys.K;
-  const long long need = (total + kResidualThreads - 1) / kResidualThreads;
-  const int grid = (int)(need < kResidualGrid ? (need > 0 ? need : 1) : kResidualGrid);
+  const int grid = residual_grid(J->n_nodes);
   if ((size_t)grid * 2 * sys.K > kNoAllocScratchDoubles) return FNLH_ERR_UNSUPPORTED;
   double* partials = nullptr;
   const int rc = scratch_address(&partials);
@@ -262,8 +300,9 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   a.x_zero = 0;
   a.partials = partials;
   a.sys = sys;
-  if (J->block == 5) k_residual<5><<<grid, kResidualThreads, 0, s>>>(a);
-  else k_residual<6><<<grid, kResidualThreads, 0, s>>>(a);
+  const int threads = 32 * std::min(sys.K, kResidualThreads / 32);
+  if (J->block == 5) k_residual<5><<<grid, threads, 0, s>>>(a);
+  else k_residual<6><<<grid, threads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
   k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(partials, grid, 2 * sys.K, norms);
   FNLH_LAUNCH_CHECK();

@@ -35,13 +35,15 @@ struct SweepArgs {
   double omega[kMaxSys];
 };
 
-// FP64: one thread per pair, blocks from global memory.
+// FP64: a CTA per 32 consecutive nodes, each warp taking whole systems for
+// them (system-major), so that the mean flow's warp runs the real-only path.
 template <int BS>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)a.row.n * a.row.K) return;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (i >= a.row.n) return;
   const SweepIO io{a.Xin, a.Xout, a.omega};
-  sweep_pair_f64<BS>(a.row, io, g, a.x_zero != 0);
+  const int nwarps = blockDim.x >> 5;
+  for (int k = threadIdx.x >> 5; k < a.row.K; k += nwarps) sweep_node_f64<BS>(a.row, io, i, k, a.x_zero != 0);
 }
 
 // FP32 arithmetic on FP32 or BF16 blocks, staged per CTA tile.
@@ -239,7 +241,8 @@ int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
   const long long count = (long long)a.row.n * a.row.K;
   if (count == 0) return FNLH_OK;
   if constexpr (sizeof(T) == 8) {
-    k_sweep_f64<BS><<<blocks_for(count, kSweepThreads), kSweepThreads, 0, s>>>(a);
+    const int warps = std::min(a.row.K, kSweepThreads / 32);
+    k_sweep_f64<BS><<<(unsigned)((a.row.n + 31) / 32), 32 * warps, 0, s>>>(a);
   } else {
     k_sweep_f32<BS, TJ><<<blocks_for(count, kSweepThreads), kSweepThreads, smem_bytes, s>>>(a);
   }

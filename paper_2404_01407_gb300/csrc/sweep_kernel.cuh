@@ -279,6 +279,66 @@ __device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& 
   finish_pair<BS, double>(R, io, (const double*)R.hess + (size_t)i * BS * BS, i, k, s);
 }
 
+// FP64, system-major tile: a CTA owns 32 consecutive nodes and each warp
+// takes whole systems for those nodes (lane = node).  The mean flow's warp
+// (system 0, omega = 0) runs a real-only path -- half the multiply-adds of the
+// complex path and a real back-substitution -- instead of carrying a zero
+// imaginary part through the complex code.
+template <int BS>
+__device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& io, int i, int k, bool x_zero) {
+  if (k != 0) {
+    sweep_pair_f64<BS>(R, io, (long long)i * R.K + k, x_zero);
+    return;
+  }
+  const double* bt = (const double*)R.Bt + (size_t)i * R.K * 2 * BS;  // system 0 slice: (re, 0) pairs
+  double sr[BS];
+#pragma unroll
+  for (int t = 0; t < BS; ++t) sr[t] = __ldg(bt + 2 * t);
+  if (!x_zero) {
+    const double* __restrict__ X = (const double*)io.Xin;
+    const double* __restrict__ offd = (const double*)R.offd;
+    const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
+    for (int p = p0; p < p1; ++p) {
+      const int j = __ldg(R.col_idx + p);
+      const double* xs = X + (size_t)j * R.K * 2 * BS;
+      double xr[BS];
+#pragma unroll
+      for (int t = 0; t < BS; ++t) xr[t] = __ldg(xs + 2 * t);
+      double J[BS * BS];
+      load_block<BS>(offd + (size_t)p * BS * BS, J);
+#pragma unroll
+      for (int r = 0; r < BS; ++r)
+#pragma unroll
+        for (int t = 0; t < BS; ++t) sr[r] -= J[r * BS + t] * xr[t];
+    }
+  }
+  const double* H = (const double*)R.hess + (size_t)i * BS * BS;
+  bool tri = true;
+#pragma unroll
+  for (int q = 0; q < BS - 1; ++q) tri = tri && (H[(q + 1) * BS + q] == 0.0);
+  double* xo = (double*)io.Xout + (size_t)i * R.K * 2 * BS;
+  if (tri) {
+#pragma unroll
+    for (int q = BS - 1; q >= 0; --q) {
+      double acc = sr[q];
+#pragma unroll
+      for (int c = q + 1; c < BS; ++c) acc -= H[q * BS + c] * sr[c];
+      sr[q] = acc / H[q * BS + q];
+    }
+#pragma unroll
+    for (int t = 0; t < BS; ++t) reinterpret_cast<double2*>(xo)[t] = make_double2(sr[t], 0.0);
+  } else {
+    Cvec<BS, double> v;
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      v.re[t] = sr[t];
+      v.im[t] = 0.0;
+    }
+    hess_solve<BS, double>(H, 0.0, v.re, v.im);
+    store_slice<BS>(xo, v);
+  }
+}
+
 // Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
 // Every thread of the CTA must call it (it synchronises).
 // Every thread of the CTA must call this (it synchronises).
