@@ -90,24 +90,6 @@ __device__ __forceinline__ void load_block(const double* __restrict__ p, double 
   }
 }
 
-// FP32 block from shared memory (staged) or global memory.
-template <int BS>
-__device__ __forceinline__ void load_block_f32(const float* p, float (&J)[BS * BS]) {
-  if constexpr ((BS * BS) % 4 == 0) {
-#pragma unroll
-    for (int q = 0; q < BS * BS / 4; ++q) {
-      const float4 f = reinterpret_cast<const float4*>(p)[q];
-      J[4 * q] = f.x;
-      J[4 * q + 1] = f.y;
-      J[4 * q + 2] = f.z;
-      J[4 * q + 3] = f.w;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < BS * BS; ++q) J[q] = p[q];
-  }
-}
-
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
@@ -341,6 +323,33 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
 
 // Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
 // Every thread of the CTA must call it (it synchronises).
+// s -= J x for one staged FP32 block, consumed row by row from shared
+// memory: six live block entries instead of thirty-six keep the register
+// count (and with it three CTAs per SM) without spilling.
+template <int BS>
+__device__ __forceinline__ void spmv_rows_smem(const float* jb, const Cvec<BS, float>& x, Cvec<BS, float>& s) {
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    float jr[BS];
+    if constexpr (BS % 2 == 0) {
+#pragma unroll
+      for (int t = 0; t < BS; t += 2) {
+        const float2 f = reinterpret_cast<const float2*>(jb + r * BS)[t / 2];
+        jr[t] = f.x;
+        jr[t + 1] = f.y;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < BS; ++t) jr[t] = jb[r * BS + t];
+    }
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      s.re[r] -= jr[t] * x.re[t];
+      s.im[r] -= jr[t] * x.im[t];
+    }
+  }
+}
+
 // Every thread of the CTA must call this (it synchronises).
 template <int BS, typename TJ>
 __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& io, long long g0, bool x_zero,
@@ -394,25 +403,27 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
           const int j = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
           load_slice<BS>(Xk + (size_t)j * stride, xn);
         }
-        float J[BS * BS];
         if (staged) {
-          load_block_f32<BS>(sJ + (size_t)(p - p_first) * BS * BS, J);
-        } else if constexpr (sizeof(TJ) == 2) {
-          const uint16_t* q = reinterpret_cast<const uint16_t*>(R.offd) + (size_t)p * BS * BS;
-#pragma unroll
-          for (int e = 0; e < BS * BS; ++e) J[e] = __uint_as_float((uint32_t)__ldg(q + e) << 16);
+          spmv_rows_smem<BS>(sJ + (size_t)(p - p_first) * BS * BS, x, s);
         } else {
-          const float* q = (const float*)R.offd + (size_t)p * BS * BS;
+          float J[BS * BS];
+          if constexpr (sizeof(TJ) == 2) {
+            const uint16_t* q = reinterpret_cast<const uint16_t*>(R.offd) + (size_t)p * BS * BS;
 #pragma unroll
-          for (int e = 0; e < BS * BS; ++e) J[e] = __ldg(q + e);
-        }
+            for (int e = 0; e < BS * BS; ++e) J[e] = __uint_as_float((uint32_t)__ldg(q + e) << 16);
+          } else {
+            const float* q = (const float*)R.offd + (size_t)p * BS * BS;
 #pragma unroll
-        for (int r = 0; r < BS; ++r)
-#pragma unroll
-          for (int t = 0; t < BS; ++t) {
-            s.re[r] -= J[r * BS + t] * x.re[t];
-            s.im[r] -= J[r * BS + t] * x.im[t];
+            for (int e = 0; e < BS * BS; ++e) J[e] = __ldg(q + e);
           }
+#pragma unroll
+          for (int r = 0; r < BS; ++r)
+#pragma unroll
+            for (int t = 0; t < BS; ++t) {
+              s.re[r] -= J[r * BS + t] * x.re[t];
+              s.im[r] -= J[r * BS + t] * x.im[t];
+            }
+        }
       }
     }
     const float* H = staged ? sH + (size_t)(i - i_first) * BS * BS : (const float*)R.hess + (size_t)i * BS * BS;
