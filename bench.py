@@ -140,12 +140,13 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """Largest value over the ranks (the job time is the slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -185,7 +186,7 @@ def run_reference(args):
     import oracle
     from paper_2404_01407_gb300 import inputs
 
-    p = inputs.config_problem(WORKLOAD)
+    p = inputs.config_problem(args.workload)
     m = p.mesh
     K = 1 + p.n_harm
     oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
@@ -199,12 +200,12 @@ def run_reference(args):
         oracle.residual(oj, m.vol, p.omega, p.b, X)
     t = time.perf_counter() - t0
     value = m.n_nodes * K * sweeps_per_step * args.steps / t
-    sample = (f"{WORKLOAD} full mesh; each step {sweeps_per_step} FP64 Jacobi sweeps + 1 residual "
+    sample = (f"{args.workload} full mesh; each step {sweeps_per_step} FP64 Jacobi sweeps + 1 residual "
               f"(Jacobian built once, untimed)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p),
+            "data": "synthetic", "config": workload_config(p, sweeps_per_step),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -214,12 +215,12 @@ def run_reference(args):
         dist.barrier()
 
 
-def workload_config(p):
+def workload_config(p, sweeps=SWEEPS):
     return {"workload": f"{p.name}: {p.mesh.dims[0]}x{p.mesh.dims[1]}x{p.mesh.dims[2]} perturbed hex passage, "
                         f"{p.mesh.n_nodes} nodes, {p.mesh.n_edges} edges, b={p.block}, mean + {p.n_harm} harmonics, "
-                        f"CFL {p.cfl:g}, {SWEEPS} FP64 block-Jacobi sweeps per step (+ Jacobian build + residual)",
+                        f"CFL {p.cfl:g}, {sweeps} FP64 block-Jacobi sweeps per step (+ Jacobian build + residual)",
             "nodes": p.mesh.n_nodes, "edges": p.mesh.n_edges, "block": p.block, "harmonics": p.n_harm,
-            "sweeps_per_step": SWEEPS, "l2": "inputs larger than L2 (J alone 0.67 GB FP64)"}
+            "sweeps_per_step": sweeps, "l2": "inputs larger than L2 (J alone 0.67 GB FP64)"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -238,7 +239,7 @@ def run_fnlh(args):
     peaks, peaks_kind = load_peaks()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    p = inputs.config_problem(WORKLOAD)
+    p = inputs.config_problem(args.workload)
     n, E, b, N = p.mesh.n_nodes, p.mesh.n_edges, p.block, p.n_harm
     K, nnz = 1 + N, 2 * E
     dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
@@ -292,7 +293,7 @@ def run_fnlh(args):
     roofline = {"bound": "alu", "kernel": "k_sweep_f64<6> (FP64 fused sweep)",
                 "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_FLOPS,
-                "traffic": NCU_TRAFFIC.get("k_sweep_f64_c2"),
+                "traffic": NCU_TRAFFIC.get(f"k_sweep_f64_{args.workload}"),
                 "peak_note": "FP64 peak from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
                              "not in MEASURED_PEAKS.json",
                 "sweep_ms": sweep_ms, "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
@@ -520,6 +521,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["c1", "c2"],
+                    help="c2 (128x64x48, the measured configuration) or c1 (16x8x8, a quick check)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -284,3 +284,86 @@ def test_complex_spectrum_block_uses_hessenberg_fallback(prec):
             y = np.linalg.solve(M, b[node, 2 * k - 1] + 1j * b[node, 2 * k])
             got = x[node, 2 * k - 1] + 1j * x[node, 2 * k]
             assert np.linalg.norm(got - y) <= tol * np.linalg.norm(y)
+
+
+def test_relax_f64_block_pseudo_time_matches_oracle():
+    """Eq. precon's block pseudo-time form (D = 0, J_ii scaled by 1 + 1/(eps CFL))."""
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p, pseudo_time=1)
+    oj = _gpu.oracle_jacobian(p, pseudo_time=1)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 30, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 30)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+
+
+def test_zero_sweeps_round_trips_the_basis():
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    x = np.random.default_rng(2).normal(size=p.b.shape)
+    X = torch.from_numpy(x.copy()).cuda()
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 0, fnlh.FNLH_F64)
+    assert np.abs(X.cpu().numpy() - x).max() <= 1e-14 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_mixed_solve_b5_and_permuted_numbering(prec):
+    """Euler blocks (b = 5) on a randomly renumbered mesh."""
+    base = inputs.problem((14, 10, 8), 5, 3, 10.0, 1.3)
+    mesh, perm = inputs.permute_mesh(base.mesh, seed=4)
+    p = inputs.Problem(mesh=mesh, q=base.q[perm], b=base.b[perm], omega=base.omega, block=5, cfl=10.0)
+    dm, J, B = _gpu.device_problem(p)
+    X = torch.empty_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40,
+                                              flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
+    assert st == fnlh.FNLH_OK
+    oj = _gpu.oracle_jacobian(p)
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+    assert np.all(true_rel <= 1.05e-8), true_rel
+
+
+def test_mixed_solve_many_harmonics():
+    """64 harmonics (the largest count): the FP32 stage layout for K = 65."""
+    p = inputs.problem((8, 6, 5), 6, 64, 20.0, 0.2)
+    dm, J, B = _gpu.device_problem(p)
+    X = torch.empty_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 20, 40,
+                                              flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
+    assert st == fnlh.FNLH_OK
+    oj = _gpu.oracle_jacobian(p)
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+    assert np.all(true_rel <= 1.05e-8), true_rel.max()
+
+
+def test_solve_reports_not_converged():
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    X = torch.zeros_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-12, 2, 3,
+                                              raise_on_error=False)
+    assert st == fnlh.FNLH_ERR_NOT_CONVERGED and checks == 3 and sweeps == 4
+    assert np.all(rel > 1e-12) and np.all(rel < 1.0)
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_BF16, fnlh.FNLH_F64])
+def test_batched_rows_other_precisions(prec):
+    rows = [inputs.problem((9, 7, 5), 6, 2, 20.0, 1.0, seeds=(1, 2, 3)),
+            inputs.problem((12, 8, 6), 6, 8, 20.0, 1.6, seeds=(4, 5, 6))]
+    dev = [(p, *_gpu.device_problem(p)) for p in rows]
+    singles = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, 9, prec)
+        singles.append(X.cpu().numpy())
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
+    fnlh.fnlh_relax_batched(batch, 9, prec, tuning=fnlh.fnlh_tuning(256, 0), ws=ws)
+    for X, ref, (p, *_rest) in zip(Xs, singles, dev):
+        if prec == fnlh.FNLH_F64:
+            # the single-row FP64 kernel solves the mean flow with a real-only path
+            err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+            assert np.all(err <= 1e-13), err
+        else:
+            assert np.array_equal(X.cpu().numpy(), ref)
