@@ -194,9 +194,13 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
                   double *norms, void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
 
 /* fnlh_solve flags */
-#define FNLH_SOLVE_ZERO_GUESS 1 /* start from x0 = 0 (X is overwritten; the first residual is B) */
+#define FNLH_SOLVE_ZERO_GUESS 1     /* start from x0 = 0 (X is overwritten; the first residual is B) */
+#define FNLH_SOLVE_MASK_CONVERGED 2 /* systems already at tol are not swept again (their x is kept) */
 
-/* Solve every system to ||r_k|| <= tol ||B_k||.  precision FNLH_F64: plain FP64
+/* Solve every system to ||r_k|| <= tol ||B_k||.  With x0 = 0 and tol = 1e-2 this is
+ * the paper's linear-solve rule (Results, Table fnlh_para: the residual drops
+ * two orders of magnitude from its initial value; max_checks and inner_sweeps
+ * bound the iterations).  precision FNLH_F64: plain FP64
  * Jacobi with an FP64 residual check every `inner_sweeps` sweeps.
  * FNLH_F32 / FNLH_BF16: defect correction -- FP64 residual r = B - A x,
  * `inner_sweeps` sweeps on A e = r with the low-precision blocks and FP32

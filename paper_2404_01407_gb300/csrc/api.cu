@@ -223,7 +223,7 @@ int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || !(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
-  if (flags & ~FNLH_SOLVE_ZERO_GUESS) return FNLH_ERR_ARG;
+  if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
   FNLH_TRY(check_systems(n_harm, omega));
   FNLH_TRY(check_prep(J, precision));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;

@@ -32,6 +32,8 @@ struct SweepArgs {
   int32_t x_zero;
   int32_t smem_floats;
   int32_t* status;  // workspace status word (bit 0: a bounded wait timed out)
+  int32_t masked;   // 0: every system is swept; 1: only the systems set in `active`
+  uint64_t active[2];
   double omega[kMaxSys];
 };
 
@@ -41,16 +43,19 @@ template <int BS>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   if (i >= a.row.n) return;
-  const SweepIO io{a.Xin, a.Xout, a.omega};
+  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr};
   const int nwarps = blockDim.x >> 5;
-  for (int k = threadIdx.x >> 5; k < a.row.K; k += nwarps) sweep_node_f64<BS>(a.row, io, i, k, a.x_zero != 0);
+  for (int k = threadIdx.x >> 5; k < a.row.K; k += nwarps) {
+    if (sys_active(io, k)) sweep_node_f64<BS>(a.row, io, i, k, a.x_zero != 0);
+    else freeze_pair<BS, double>(a.row, io, i, k, a.x_zero != 0);
+  }
 }
 
 // FP32 arithmetic on FP32 or BF16 blocks, staged per CTA tile.
 template <int BS, typename TJ>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_f32(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(16) float smem[];
-  const SweepIO io{a.Xin, a.Xout, a.omega};
+  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr};
   sweep_tile_f32<BS, TJ>(a.row, io, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
 }
 
@@ -254,7 +259,8 @@ int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
 // (or from zero when x_zero), returns the buffer holding the result.
 template <int BS, typename TJ, typename T>
 int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, const T* Bt, T* x0, T* x1,
-               int sweeps, int x_zero, int32_t* status, cudaStream_t s, T** result) {
+               int sweeps, int x_zero, int32_t* status, cudaStream_t s, T** result,
+               const uint64_t* active = nullptr) {
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.row.n = m->n_nodes;
@@ -267,6 +273,9 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.row.vol = m->vol;
   a.row.Bt = Bt;
   a.status = status;
+  a.masked = active ? 1 : 0;
+  a.active[0] = active ? active[0] : ~0ull;
+  a.active[1] = active ? active[1] : ~0ull;
   for (int k = 0; k < kMaxSys; ++k) a.omega[k] = sys.omega[k];
   size_t smem = 0;
   int rc = FNLH_OK;
@@ -370,6 +379,8 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   int checks = 0, sweeps = 0;
   bool conv = false;
   const bool mixed = precision != FNLH_F64;
+  const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
+  uint64_t active[2] = {~0ull, ~0ull};
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
   if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
   if (!mixed) {
@@ -395,10 +406,14 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     rc = check_norms(hn, K, tol, &ck, checks == 0, &conv);
     ++checks;
     if (rc || conv || checks >= max_checks) break;
+    if (masking)  // converged systems are frozen for the following sweeps
+      for (int k = 0; k < K; ++k)
+        if (ck.rel[k] <= tol) active[k >> 6] &= ~(1ull << (k & 63));
+    const uint64_t* act = masking ? active : nullptr;
     T* res = nullptr;
     if (mixed) {
       // inner: A~ e = r~ from e = 0 (v1/v2 ping-pong), then x += Q e in FP64
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res, act))) return rc;
       const long long count = (long long)n * K;
       if (count > 0) {
         k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X);
@@ -406,7 +421,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       }
     } else {
       T* other = (cur == v1) ? v2 : v1;
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res, act))) return rc;
       cur = res;
       if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 0, s))) return rc;
     }
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched(const __grid
     int r = 0;
     while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
     const BatchRow& D = a.row[r];
-    const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega};
+    const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, nullptr};
     const long long g0 = (t - D.tile0) * blockDim.x;
     if constexpr (sizeof(T) == 8) {
       const long long g = g0 + threadIdx.x;

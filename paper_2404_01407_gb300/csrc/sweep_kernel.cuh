@@ -221,7 +221,23 @@ struct SweepIO {
   const void* Xin;       // [n][K][b] complex (not read when x_zero)
   void* Xout;            // [n][K][b] complex
   const double* omega;   // [K], omega[0] = 0
+  const uint64_t* active;  // bit k set: system k is swept; null: every system
 };
+
+__device__ __forceinline__ bool sys_active(const SweepIO& io, int k) {
+  return io.active == nullptr || ((io.active[k >> 6] >> (k & 63)) & 1ull);
+}
+
+// A frozen (converged) system keeps its iterate: copy the slice through the
+// ping-pong, or write zeros on a sweep that starts from zero.
+template <int BS, typename T>
+__device__ __forceinline__ void freeze_pair(const TileRow& R, const SweepIO& io, int i, int k, bool x_zero) {
+  const size_t off = ((size_t)i * R.K + k) * 2 * BS;
+  T* out = (T*)io.Xout + off;
+  const T* in = (const T*)io.Xin + off;
+#pragma unroll
+  for (int t = 0; t < 2 * BS; ++t) out[t] = x_zero ? T(0) : in[t];
+}
 
 // Shifted Hessenberg solve + store for one pair, shared by both forms.
 template <int BS, typename T, typename TH>
@@ -383,7 +399,10 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
     stage_f32(sH, (const float*)R.hess + (size_t)i_first * BS * BS, nodes * BS * BS, v4);
   }
   __syncthreads();
-  if (g < total) {
+  if (g < total && !sys_active(io, (int)g - (int)fdiv(g, R.divK) * R.K)) {
+    const int i = (int)fdiv(g, R.divK);
+    freeze_pair<BS, float>(R, io, i, (int)g - i * R.K, x_zero);
+  } else if (g < total) {
     const int i = (int)fdiv(g, R.divK);
     const int k = (int)g - i * R.K;
     if (!x_zero) {

@@ -276,6 +276,7 @@ def fnlh_residual(dmesh, J, omega, B, X, r=None, norms=None, ws=None, stream=Non
 
 
 FNLH_SOLVE_ZERO_GUESS = 1
+FNLH_SOLVE_MASK_CONVERGED = 2
 
 
 def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, ws=None, stream=None,
