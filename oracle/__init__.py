@@ -15,8 +15,9 @@ Parity pins (tests/test_oracle_pins.py) tie every function here to something
 other than itself: the textbook Euler flux Jacobian and its eigenvalues, an
 eigendecomposition of |A|, complex-step derivatives of a frozen-dissipation
 first-order residual, closed forms on a uniform state, dense direct solves,
-the real 2x2-block form of Eq. matrix_z_real, and hand-solvable one- and
-two-node systems.
+the real 2x2-block form of Eq. matrix_z_real, hand-solvable one- and
+two-node systems, and (phase-lagged periodic edges) the equivalence of one
+passage with phase lag to a ring of passages with plain periodicity.
 """
 
 from __future__ import annotations
@@ -40,6 +41,7 @@ EPS = 0.6
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i8p = np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -77,8 +79,11 @@ def _bind(lib):
         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, _i32p, _i32p,
         _f64p, _f64p, _f64p]
     lib.oracle_build_jacobian.restype = ctypes.c_int
+    lib.oracle_phase_sides.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i8p, _i32p, _i8p]
+    lib.oracle_phase_sides.restype = ctypes.c_int
+    # n, b, n_harm, row_ptr, col_idx, offd, diag, D, vol, omega, side, sigma, B
     common = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p,
-              _f64p, _f64p, _f64p]
+              _f64p, _f64p, ctypes.c_void_p, ctypes.c_void_p, _f64p]
     lib.oracle_jacobi.argtypes = common + [_f64p, ctypes.c_int]
     lib.oracle_jacobi.restype = ctypes.c_int
     lib.oracle_residual.argtypes = common + [_f64p, ctypes.c_void_p, _f64p]
@@ -136,11 +141,13 @@ def spectral_radius(q, n, gamma: float = GAMMA) -> float:
 
 
 class Jacobian:
-    """Oracle Jacobian: CSR pattern, off-diagonal and diagonal blocks, D."""
+    """Oracle Jacobian: CSR pattern, off-diagonal and diagonal blocks, D, and
+    (periodic meshes) the passage offset `side` [nnz] of every CSR entry."""
 
-    def __init__(self, row_ptr, col_idx, offd, diag, D, block):
+    def __init__(self, row_ptr, col_idx, offd, diag, D, block, side=None):
         self.row_ptr, self.col_idx, self.offd, self.diag, self.D = row_ptr, col_idx, offd, diag, D
         self.block = block
+        self.side = side
 
     @property
     def n_nodes(self):
@@ -151,9 +158,24 @@ class Jacobian:
         return int(self.col_idx.shape[0])
 
 
+def phase_sides(n_nodes, edge_nodes, periodic) -> np.ndarray:
+    """Passage offset (-1, 0, +1) of the neighbour of every CSR entry, from the
+    per-edge offsets of the edges' second nodes."""
+    en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
+    E = en.shape[0]
+    per = np.ascontiguousarray(periodic, dtype=np.int8).reshape(E)
+    row_ptr = np.zeros(n_nodes + 1, dtype=np.int32)
+    side = np.zeros(max(2 * E, 1), dtype=np.int8)
+    rc = _load().oracle_phase_sides(n_nodes, E, en.ravel(), per if E else np.zeros(1, np.int8), row_ptr, side)
+    if rc != 0:
+        raise ValueError(f"oracle_phase_sides failed ({rc})")
+    return side[: 2 * E].copy()
+
+
 def build_jacobian(n_nodes, edge_nodes, normals, q, cfl, gamma=GAMMA, delta=DELTA,
-                   pseudo_block=False, eps=EPS) -> Jacobian:
-    """First-order edge Jacobian J, diagonal blocks and pseudo-time diagonal D."""
+                   pseudo_block=False, eps=EPS, periodic=None) -> Jacobian:
+    """First-order edge Jacobian J, diagonal blocks and pseudo-time diagonal D
+    (periodic: per-edge passage offsets of a phase-lagged periodic mesh)."""
     q = _f64(q)
     b = q.shape[1]
     en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
@@ -168,31 +190,44 @@ def build_jacobian(n_nodes, edge_nodes, normals, q, cfl, gamma=GAMMA, delta=DELT
                                       col_idx, offd, diag, D)
     if rc != 0:
         raise ValueError(f"oracle_build_jacobian failed ({rc})")
+    side = None if periodic is None else phase_sides(n_nodes, en, periodic)
     return Jacobian(row_ptr, col_idx[: 2 * E].copy(), offd[: 2 * E * b * b].reshape(2 * E, b, b),
-                    diag.reshape(n_nodes, b, b), D, b)
+                    diag.reshape(n_nodes, b, b), D, b, side)
 
 
-def _sys_args(jac: Jacobian, vol, omega):
+def _sys_args(jac: Jacobian, vol, omega, sigma, keep):
+    """Marshalled arguments; `keep` holds the arrays behind raw pointers."""
     b = jac.block
     offd = _f64(jac.offd).ravel()
     if offd.size == 0:
         offd = np.zeros(1)
     col = jac.col_idx if jac.col_idx.size else np.zeros(1, dtype=np.int32)
-    return (jac.n_nodes, b, int(np.asarray(omega).shape[0]), jac.row_ptr, col, offd,
-            _f64(jac.diag).ravel(), _f64(jac.D), _f64(vol), _f64(np.atleast_1d(omega)) if len(omega) else np.zeros(1))
+    n_harm = int(np.asarray(omega).shape[0])
+    side_p = sigma_p = None
+    if jac.side is not None and sigma is not None and n_harm > 0:
+        side = np.ascontiguousarray(jac.side, dtype=np.int8)
+        sig = _f64(np.atleast_1d(sigma))
+        if sig.shape[0] != n_harm:
+            raise ValueError("sigma needs one phase angle per harmonic")
+        keep += [side, sig]
+        side_p, sigma_p = side.ctypes.data_as(ctypes.c_void_p), sig.ctypes.data_as(ctypes.c_void_p)
+    return (jac.n_nodes, b, n_harm, jac.row_ptr, col, offd, _f64(jac.diag).ravel(), _f64(jac.D), _f64(vol),
+            _f64(np.atleast_1d(omega)) if len(omega) else np.zeros(1), side_p, sigma_p)
 
 
-def jacobi(jac: Jacobian, vol, omega, B, sweeps: int, X0=None) -> np.ndarray:
-    """x after `sweeps` undamped block-Jacobi sweeps from X0 (zero if None)."""
+def jacobi(jac: Jacobian, vol, omega, B, sweeps: int, X0=None, sigma=None) -> np.ndarray:
+    """x after `sweeps` undamped block-Jacobi sweeps from X0 (zero if None);
+    sigma: inter-blade phase angle per harmonic (periodic meshes)."""
     B = _f64(B)
     X = np.zeros_like(B) if X0 is None else _f64(X0).copy()
-    rc = _load().oracle_jacobi(*_sys_args(jac, vol, omega), B.ravel(), X.reshape(-1), int(sweeps))
+    keep = []
+    rc = _load().oracle_jacobi(*_sys_args(jac, vol, omega, sigma, keep), B.ravel(), X.reshape(-1), int(sweeps))
     if rc != 0:
         raise FloatingPointError("singular diagonal block")
     return X
 
 
-def residual(jac: Jacobian, vol, omega, B, X, want_r: bool = False):
+def residual(jac: Jacobian, vol, omega, B, X, want_r: bool = False, sigma=None):
     """Returns (norms[K,2] = (||r_k||^2, ||B_k||^2), r or None)."""
     B = _f64(B)
     X = _f64(X)
@@ -200,23 +235,24 @@ def residual(jac: Jacobian, vol, omega, B, X, want_r: bool = False):
     norms = np.zeros(2 * K)
     r = np.zeros_like(B) if want_r else None
     rp = r.ctypes.data_as(ctypes.c_void_p) if want_r else None
-    _load().oracle_residual(*_sys_args(jac, vol, omega), B.ravel(), X.ravel(), rp, norms)
+    keep = []
+    _load().oracle_residual(*_sys_args(jac, vol, omega, sigma, keep), B.ravel(), X.ravel(), rp, norms)
     return norms.reshape(K, 2), r
 
 
-def rel_residuals(jac: Jacobian, vol, omega, B, X) -> np.ndarray:
+def rel_residuals(jac: Jacobian, vol, omega, B, X, sigma=None) -> np.ndarray:
     """||B_k - A_k x_k|| / ||B_k|| per system k (mean first)."""
-    norms, _ = residual(jac, vol, omega, B, X)
+    norms, _ = residual(jac, vol, omega, B, X, sigma=sigma)
     return np.sqrt(norms[:, 0] / np.maximum(norms[:, 1], 1e-300))
 
 
-def solve_to_tol(jac: Jacobian, vol, omega, B, tol: float, chunk: int = 10, max_sweeps: int = 100000):
+def solve_to_tol(jac: Jacobian, vol, omega, B, tol: float, chunk: int = 10, max_sweeps: int = 100000, sigma=None):
     """Plain FP64 Jacobi until every system's relative residual <= tol."""
     X = np.zeros_like(_f64(B))
     done = 0
     while done < max_sweeps:
-        X = jacobi(jac, vol, omega, B, chunk, X0=X)
+        X = jacobi(jac, vol, omega, B, chunk, X0=X, sigma=sigma)
         done += chunk
-        if np.all(rel_residuals(jac, vol, omega, B, X) <= tol):
+        if np.all(rel_residuals(jac, vol, omega, B, X, sigma=sigma) <= tol):
             break
     return X, done

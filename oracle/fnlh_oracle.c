@@ -43,6 +43,14 @@
  *  - The linear residual r_k = B_k - A_k x_k and its 2-norm, the quantity
  *    whose drop the paper's linear-solve stopping rule tests (Results,
  *    Table fnlh_para).
+ *  - Phase-lagged periodic boundaries (Eq. lhs_lin and the text around
+ *    Eq. precon_linear: the inter-blade phase angle changes each harmonic's
+ *    LHS but not its sparsity).  A periodic edge joins node i to the image of
+ *    node j in the neighbouring blade passage; the harmonic-l perturbation of
+ *    that image is e^{i s sigma_l} x_j, s = +1 (next passage) or -1
+ *    (previous).  So the off-diagonal term of harmonic l across such an edge
+ *    is J_ij e^{i s sigma_l} x_j: J itself is unchanged and shared, the mean
+ *    flow (plain periodicity) carries no phase.
  *
  * Layout: X, B, r are real [n][C][b], C = 1 + 2N; column 0 is the mean flow,
  * columns 2l-1 / 2l are Re / Im of harmonic l (omega[l-1]).  Off-diagonal
@@ -206,6 +214,20 @@ static int make_neighbours(int n, int E, const int32_t *edge_nodes, int32_t *row
     return 0;
 }
 
+/* Passage offset of the neighbour of every CSR entry (same order as the
+ * col_idx that oracle_build_jacobian writes).  periodic[e] in {-1, 0, +1} is
+ * the passage of the edge's second node as seen from its first; seen from
+ * the second node the offset is the opposite. */
+int oracle_phase_sides(int n, int E, const int32_t *edge_nodes, const int8_t *periodic, int32_t *row_ptr,
+                       int8_t *side)
+{
+    nbr_t *nb = NULL;
+    if (make_neighbours(n, E, edge_nodes, row_ptr, &nb) != 0) return -2;
+    for (int p = 0; p < 2 * E; p++) side[p] = (int8_t)(nb[p].sgn * periodic[nb[p].e]);
+    free(nb);
+    return 0;
+}
+
 /* ------------------------------------------------------- Jacobian build */
 
 int oracle_build_jacobian(int n, int E, int b, const int32_t *edge_nodes, const double *normals,
@@ -330,12 +352,49 @@ static int lu_solve_cplx(int b, cplx *M, cplx *s)
 
 /* -------------------------------------------------------------- Jacobi */
 
+/* S -= sum_j J_ij x_j over row i for every column of the [C][b] row S.  With
+ * side != NULL, harmonic l takes x_j times e^{i side[p] sigma[l-1]} on the
+ * entries of periodic edges (phase-lagged boundary); the mean flow never. */
+static void subtract_offd(int i, int b, int n_harm, const int32_t *row_ptr, const int32_t *col_idx,
+                          const double *offd, const int8_t *side, const double *sigma, const double *X,
+                          double *S)
+{
+    const int C = 1 + 2 * n_harm, bb = b * b;
+    const size_t row = (size_t)C * b;
+    for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
+        const double *Jij = offd + (size_t)p * bb;
+        const double *Xj = X + (size_t)col_idx[p] * row;
+        const int s = side ? side[p] : 0;
+        for (int c = 0; c < C; c++) {
+            double xs[MAXB];
+            for (int t = 0; t < b; t++) xs[t] = Xj[c * b + t];
+            if (s != 0 && c > 0) {
+                /* column c is Re (odd c) or Im (even c) of harmonic l */
+                const int l = (c + 1) / 2;
+                const double ang = s * sigma[l - 1];
+                const double cs = cos(ang), sn = sin(ang);
+                for (int t = 0; t < b; t++) {
+                    const double re = Xj[(2 * l - 1) * b + t], im = Xj[(2 * l) * b + t];
+                    xs[t] = (c % 2 == 1) ? cs * re - sn * im : sn * re + cs * im;
+                }
+            }
+            for (int r = 0; r < b; r++) {
+                double acc = 0.0;
+                for (int t = 0; t < b; t++) acc += Jij[r * b + t] * xs[t];
+                S[c * b + r] -= acc;
+            }
+        }
+    }
+}
+
 /* One undamped block-Jacobi sweep per iteration, `sweeps` iterations;
- * X holds x^0 on entry and x^sweeps on return.  Returns -1 on a singular
+ * X holds x^0 on entry and x^sweeps on return.  side / sigma (nullable):
+ * phase-lagged periodic edges (subtract_offd).  Returns -1 on a singular
  * diagonal block. */
 int oracle_jacobi(int n, int b, int n_harm, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *offd, const double *diag, const double *D, const double *vol,
-                  const double *omega, const double *B, double *X, int sweeps)
+                  const double *omega, const int8_t *side, const double *sigma, const double *B, double *X,
+                  int sweeps)
 {
     const int C = 1 + 2 * n_harm, bb = b * b;
     const size_t row = (size_t)C * b;
@@ -347,16 +406,7 @@ int oracle_jacobi(int n, int b, int n_harm, const int32_t *row_ptr, const int32_
             double S[(1 + 2 * 64) * MAXB];
             const double *Bi = B + (size_t)i * row;
             for (size_t t = 0; t < row; t++) S[t] = Bi[t];
-            for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
-                const double *Jij = offd + (size_t)p * bb;
-                const double *Xj = X + (size_t)col_idx[p] * row;
-                for (int c = 0; c < C; c++)
-                    for (int r = 0; r < b; r++) {
-                        double acc = 0.0;
-                        for (int t = 0; t < b; t++) acc += Jij[r * b + t] * Xj[c * b + t];
-                        S[c * b + r] -= acc;
-                    }
-            }
+            subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, X, S);
             const double *Pi = diag + (size_t)i * bb;
             double *Yi = Xn + (size_t)i * row;
             /* mean flow: real system (omega = 0) */
@@ -392,7 +442,8 @@ int oracle_jacobi(int n, int b, int n_harm, const int32_t *row_ptr, const int32_
  * node order).  r may be NULL. */
 int oracle_residual(int n, int b, int n_harm, const int32_t *row_ptr, const int32_t *col_idx,
                     const double *offd, const double *diag, const double *D, const double *vol,
-                    const double *omega, const double *B, const double *X, double *r, double *norms)
+                    const double *omega, const int8_t *side, const double *sigma, const double *B,
+                    const double *X, double *r, double *norms)
 {
     const int C = 1 + 2 * n_harm, K = 1 + n_harm, bb = b * b;
     const size_t row = (size_t)C * b;
@@ -403,16 +454,7 @@ int oracle_residual(int n, int b, int n_harm, const int32_t *row_ptr, const int3
         const double *Bi = B + (size_t)i * row;
         const double *Xi = X + (size_t)i * row;
         for (size_t t = 0; t < row; t++) R[t] = Bi[t];
-        for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
-            const double *Jij = offd + (size_t)p * bb;
-            const double *Xj = X + (size_t)col_idx[p] * row;
-            for (int c = 0; c < C; c++)
-                for (int rr = 0; rr < b; rr++) {
-                    double acc = 0.0;
-                    for (int t = 0; t < b; t++) acc += Jij[rr * b + t] * Xj[c * b + t];
-                    R[c * b + rr] -= acc;
-                }
-        }
+        subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, X, R);
         const double *Pi = diag + (size_t)i * bb;
         for (int c = 0; c < C; c++)
             for (int rr = 0; rr < b; rr++) {

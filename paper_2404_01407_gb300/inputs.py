@@ -17,7 +17,11 @@ compressor / turbine / LPC sizes of the Results section):
   in node order, then y-edges, then z-edges); the dual-face normal of edge
   (i, j) is ``x_j - x_i``; the control volume is the product over the three
   axes of half the distance between the two axis neighbours (one-sided half
-  distance on the lattice boundary).
+  distance on the lattice boundary).  Periodic variant (a blade passage of
+  pitch ny): every node of the last y-layer gets one more edge, to the first
+  layer's node seen one pitch further along y (normal ``x_j + ny e_y - x_i``),
+  flagged +1 in ``periodic``; inter-blade phase angles of harmonic l are
+  ``2 pi l m / N_b`` (m = 3, N_b = 8 by default).
 * state (seed 2): gamma = 1.4, p = 1/gamma, rho = 1 + U(-0.02, 0.02),
   Mach = 0.5 + U(-0.05, 0.05) along +x, v = w = 0; with 6 equations the sixth
   conserved variable is rho * 0.01 (a constant SA working variable).
@@ -44,9 +48,12 @@ class Mesh:
 
     dims: tuple
     positions: np.ndarray  # [n][3] f64
-    edge_nodes: np.ndarray  # [E][2] int32, edge_nodes[e] = (i, j), i < j
+    edge_nodes: np.ndarray  # [E][2] int32, edge_nodes[e] = (i, j)
     normals: np.ndarray  # [E][3] f64, dual-face normal n_ij (from i to j)
     vol: np.ndarray  # [n] f64
+    # [E] int8 or None: +1 when node j of the edge is seen from node i across
+    # the pitchwise periodic boundary (its image in the next blade passage)
+    periodic: np.ndarray = None
 
     @property
     def n_nodes(self) -> int:
@@ -57,8 +64,11 @@ class Mesh:
         return int(self.edge_nodes.shape[0])
 
 
-def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1) -> Mesh:
-    """Perturbed hex lattice treated as an unstructured edge mesh."""
+def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1, periodic_y: bool = False) -> Mesh:
+    """Perturbed hex lattice treated as an unstructured edge mesh.  With
+    periodic_y the passage repeats with pitch ny along y: edges join every
+    node of the last y-layer to the image (y + ny) of the node of the first
+    layer, flagged in `periodic`."""
     n = nx * ny * nz
     rng = np.random.default_rng(seed)
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
@@ -78,6 +88,14 @@ def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1) -> 
     else:
         en = np.zeros((0, 2), dtype=np.int64)
     normals = pos[en[:, 1]] - pos[en[:, 0]] if len(en) else np.zeros((0, 3))
+    periodic = None
+    if periodic_y and ny > 2:
+        top, bot = ids[:, -1, :].ravel(), ids[:, 0, :].ravel()
+        pen = np.stack([top, bot], axis=1)
+        pnorm = (pos[bot] + np.array([0.0, float(ny), 0.0])) - pos[top]
+        periodic = np.concatenate([np.zeros(len(en), np.int8), np.ones(len(pen), np.int8)])
+        en = np.concatenate([en, pen], axis=0)
+        normals = np.concatenate([normals, pnorm], axis=0)
 
     # control volume: product over axes of half the neighbour span
     p3 = pos.reshape(nz, ny, nx, 3)
@@ -105,6 +123,7 @@ def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1) -> 
         edge_nodes=np.ascontiguousarray(en, dtype=np.int32),
         normals=np.ascontiguousarray(normals, dtype=np.float64),
         vol=np.ascontiguousarray(vol.ravel(), dtype=np.float64),
+        periodic=periodic,
     )
 
 
@@ -130,8 +149,11 @@ def permute_mesh(mesh: Mesh, seed: int = 4) -> tuple[Mesh, np.ndarray]:
     swap = en[:, 0] > en[:, 1]
     normals = np.where(swap[:, None], -mesh.normals, mesh.normals)
     en = np.sort(en, axis=1)
+    periodic = None
+    if mesh.periodic is not None:  # the offset is seen from the edge's first node
+        periodic = np.where(swap, -mesh.periodic, mesh.periodic).astype(np.int8)
     return Mesh(dims=mesh.dims, positions=mesh.positions[perm], edge_nodes=en.astype(np.int32),
-                normals=np.ascontiguousarray(normals), vol=mesh.vol[perm].copy()), perm
+                normals=np.ascontiguousarray(normals), vol=mesh.vol[perm].copy(), periodic=periodic), perm
 
 
 def flow_state(n: int, block: int, seed: int = 2, uniform: bool = False) -> np.ndarray:
@@ -183,6 +205,8 @@ class Problem:
     cfl: float
     name: str = ""
     extra: dict = field(default_factory=dict)
+    # inter-blade phase angle of each harmonic (phase-lagged periodicity), or None
+    phase: np.ndarray = None
 
     @property
     def n_harm(self) -> int:
@@ -193,11 +217,21 @@ class Problem:
         return 1 + 2 * self.n_harm
 
 
-def problem(dims, block, n_harm, cfl, omega_base=1.0, seeds=(1, 2, 3), name="") -> Problem:
-    mesh = hex_mesh(*dims, seed=seeds[0])
+def phases(n_harm: int, blades: int = 8, nodal: int = 3) -> np.ndarray:
+    """Inter-blade phase angles sigma_l = 2 pi l m / N_b of harmonic l for a
+    disturbance of nodal diameter m on N_b blades."""
+    return 2.0 * np.pi * nodal * np.arange(1, n_harm + 1, dtype=np.float64) / blades
+
+
+def problem(dims, block, n_harm, cfl, omega_base=1.0, seeds=(1, 2, 3), name="", periodic=False,
+            phase=None) -> Problem:
+    mesh = hex_mesh(*dims, seed=seeds[0], periodic_y=periodic)
     q = flow_state(mesh.n_nodes, block, seed=seeds[1])
     b = rhs(mesh.n_nodes, block, n_harm, seed=seeds[2])
-    return Problem(mesh=mesh, q=q, b=b, omega=omegas(n_harm, omega_base), block=block, cfl=cfl, name=name)
+    if periodic and phase is None:
+        phase = phases(n_harm)
+    return Problem(mesh=mesh, q=q, b=b, omega=omegas(n_harm, omega_base), block=block, cfl=cfl, name=name,
+                   phase=None if phase is None else np.asarray(phase, dtype=np.float64))
 
 
 # Workload table: the five configurations of the measurement plan.

@@ -19,8 +19,8 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "fnlh_oracle.c")
 
 MUTATIONS = {
     "offd_sign_in_sweep": ("S[c * b + r] -= acc;", "S[c * b + r] += acc;"),
-    "transposed_block_in_sweep": ("acc += Jij[r * b + t] * Xj[c * b + t];",
-                                  "acc += Jij[t * b + r] * Xj[c * b + t];"),
+    "transposed_block_in_sweep": ("acc += Jij[r * b + t] * xs[t];",
+                                  "acc += Jij[t * b + r] * xs[t];"),
     "omega_sign_in_sweep": ("cplx shift = D[i] + I * omega[k - 1] * vol[i];",
                             "cplx shift = D[i] - I * omega[k - 1] * vol[i];"),
     "re_im_swapped_in_sweep": ("yc[r] = S[(2 * k - 1) * b + r] + I * S[(2 * k) * b + r];",
@@ -40,6 +40,12 @@ MUTATIONS = {
     "residual_without_D": ("acc += D[i] * Xi[c * b + rr];", ""),
     "residual_transposed_diag": ("acc += Pi[rr * b + t] * Xi[c * b + t];",
                                  "acc += Pi[t * b + rr] * Xi[c * b + t];"),
+    "phase_sign_flipped": ("const double ang = s * sigma[l - 1];", "const double ang = -s * sigma[l - 1];"),
+    "phase_rotation_re_sign": ("xs[t] = (c % 2 == 1) ? cs * re - sn * im : sn * re + cs * im;",
+                               "xs[t] = (c % 2 == 1) ? cs * re + sn * im : sn * re + cs * im;"),
+    "phase_side_ignores_direction": ("side[p] = (int8_t)(nb[p].sgn * periodic[nb[p].e]);",
+                                     "side[p] = (int8_t)(periodic[nb[p].e]);"),
+    "phase_im_part_unrotated": (": sn * re + cs * im;", ": im;"),
     "sylvester_wrong_index": ("double am = A[t * b + c] - ((t == c) ? lam[m] : 0.0);",
                               "double am = A[c * b + t] - ((t == c) ? lam[m] : 0.0);"),
 }

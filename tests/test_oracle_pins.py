@@ -19,6 +19,11 @@ paper or by mathematics:
   2x2-block system of Eq. matrix_z_real gives the same solution; a harmonic
   with omega = 0 reproduces the mean flow exactly.
 * Residual: B - A x from a dense matrix-vector product.
+* Phase-lagged periodic edges (Eq. lhs_lin: the inter-blade phase angle
+  changes each harmonic's LHS): one passage with phase lag sigma = 2 pi m / P
+  behaves exactly like a ring of P identical passages joined by plain
+  periodic edges whose right-hand side advances by e^{i sigma} per passage --
+  sweep by sweep for Jacobi, and entry by entry for the residual.
 """
 
 import numpy as np
@@ -443,3 +448,110 @@ def test_residual_matches_dense_product():
         assert np.allclose(rs[k], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
         assert np.isclose(norms[k, 0], np.vdot(ref, ref).real, rtol=1e-12)
         assert np.isclose(norms[k, 1], np.vdot(bs[k], bs[k]).real, rtol=1e-12)
+
+
+# ------------------------------------------------ phase-lagged periodicity
+
+RING_P = 5
+RING_M = (1, 2, 3)  # nodal diameters of the three harmonics: sigma_l = 2 pi m_l / P
+
+
+def passage_problem(block=6):
+    mesh = inputs.hex_mesh(3, 4, 2, seed=11, periodic_y=True)
+    q = inputs.flow_state(mesh.n_nodes, block, seed=12)
+    jac = oracle.build_jacobian(mesh.n_nodes, mesh.edge_nodes, mesh.normals, q, 20.0,
+                                periodic=mesh.periodic)
+    n_harm = len(RING_M)
+    B = inputs.rhs(mesh.n_nodes, block, n_harm, seed=13)
+    om = inputs.omegas(n_harm, 0.9)
+    sigma = 2.0 * np.pi * np.asarray(RING_M, dtype=np.float64) / RING_P
+    return mesh, q, jac, B, om, sigma
+
+
+def ring_of_passages(mesh, q, P):
+    """P copies of the passage side by side; every periodic edge of copy p
+    becomes an ordinary edge to the neighbouring copy (the last wraps to the
+    first), with the passage's own normals, volumes and state."""
+    n = mesh.n_nodes
+    en, per = mesh.edge_nodes.astype(np.int64), mesh.periodic.astype(np.int64)
+    edges = []
+    for p in range(P):
+        a = en[:, 0] + p * n
+        c = en[:, 1] + ((p + per) % P) * n
+        edges.append(np.stack([a, c], axis=1))
+    ring_en = np.concatenate(edges).astype(np.int32)
+    ring_normals = np.tile(mesh.normals, (P, 1))
+    return ring_en, ring_normals, np.tile(mesh.vol, P), np.tile(q, (P, 1))
+
+
+def phase_shift(X, n_harm, sigma, P):
+    """Ring vector whose passage p is passage vector X times e^{i p sigma_l}
+    (harmonic l); the mean flow is repeated unchanged."""
+    out = []
+    for p in range(P):
+        Y = X.copy()
+        for l in range(1, n_harm + 1):
+            z = (X[:, 2 * l - 1] + 1j * X[:, 2 * l]) * np.exp(1j * p * sigma[l - 1])
+            Y[:, 2 * l - 1], Y[:, 2 * l] = z.real, z.imag
+        out.append(Y)
+    return np.concatenate(out, axis=0)
+
+
+def test_phase_sides_follow_edge_direction():
+    mesh, q, jac, B, om, sigma = passage_problem()
+    side = jac.side
+    assert side.dtype == np.int8 and side.shape == (jac.nnz,)
+    owner = np.repeat(np.arange(mesh.n_nodes), np.diff(jac.row_ptr))
+    nx, ny, nz = mesh.dims
+    yj = lambda i: (i // nx) % ny  # noqa: E731
+    for p in range(jac.nnz):
+        i, j = owner[p], jac.col_idx[p]
+        want = 1 if (yj(i) == ny - 1 and yj(j) == 0) else (-1 if (yj(i) == 0 and yj(j) == ny - 1) else 0)
+        assert side[p] == want, (i, j)
+    assert (side == 1).sum() == (side == -1).sum() == nx * nz
+
+
+@pytest.mark.parametrize("sweeps", [1, 3, 12])
+def test_phase_lagged_jacobi_equals_ring(sweeps):
+    mesh, q, jac, B, om, sigma = passage_problem()
+    n, P, N = mesh.n_nodes, RING_P, len(om)
+    ren, rnorm, rvol, rq = ring_of_passages(mesh, q, P)
+    rjac = oracle.build_jacobian(n * P, ren, rnorm, rq, 20.0)
+    X0 = np.random.default_rng(14).normal(size=B.shape)
+    got = oracle.jacobi(jac, mesh.vol, om, B, sweeps, X0=X0, sigma=sigma)
+    ring = oracle.jacobi(rjac, rvol, om, phase_shift(B, N, sigma, P), sweeps, X0=phase_shift(X0, N, sigma, P))
+    ref = phase_shift(got, N, sigma, P)
+    assert np.allclose(ring, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    # the phase matters: plain periodicity (sigma = 0) is a different iterate
+    plain = oracle.jacobi(jac, mesh.vol, om, B, sweeps, X0=X0)
+    assert np.abs(plain[:, 1:] - got[:, 1:]).max() > 1e-3 * np.abs(got).max()
+    assert np.array_equal(plain[:, 0], got[:, 0])  # the mean flow carries no phase
+
+
+def test_phase_lagged_solution_is_ring_solution():
+    """Converged single passage = dense direct solve of the ring, passage 0."""
+    mesh, q, jac, B, om, sigma = passage_problem(block=5)
+    n, P, N, b = mesh.n_nodes, RING_P, len(om), jac.block
+    ren, rnorm, rvol, rq = ring_of_passages(mesh, q, P)
+    rjac = oracle.build_jacobian(n * P, ren, rnorm, rq, 20.0)
+    X, _ = oracle.solve_to_tol(jac, mesh.vol, om, B, tol=1e-15, chunk=50, max_sweeps=3000, sigma=sigma)
+    bring = _dense.split_systems(phase_shift(B, N, sigma, P), N)
+    got = _dense.split_systems(X, N)
+    for k, w in enumerate([0.0] + list(om)):
+        A = _dense.dense_operator(rjac.row_ptr, rjac.col_idx, rjac.offd, rjac.diag, rjac.D, rvol, w)
+        xr = np.linalg.solve(A, bring[k])[: n * b]
+        assert np.linalg.norm(got[k] - xr) <= 1e-12 * np.linalg.norm(xr), k
+
+
+def test_phase_lagged_residual_equals_ring():
+    mesh, q, jac, B, om, sigma = passage_problem()
+    n, P, N = mesh.n_nodes, RING_P, len(om)
+    ren, rnorm, rvol, rq = ring_of_passages(mesh, q, P)
+    rjac = oracle.build_jacobian(n * P, ren, rnorm, rq, 20.0)
+    X = np.random.default_rng(15).normal(size=B.shape)
+    norms, r = oracle.residual(jac, mesh.vol, om, B, X, want_r=True, sigma=sigma)
+    rnorms, rr = oracle.residual(rjac, rvol, om, phase_shift(B, N, sigma, P), phase_shift(X, N, sigma, P),
+                                 want_r=True)
+    ref = phase_shift(r, N, sigma, P)
+    assert np.allclose(rr, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert np.allclose(rnorms, P * norms, rtol=1e-12)
