@@ -10,8 +10,10 @@ updates per second (n K sweeps / step time), whole job.
 
 Extra sections on the same line: the mixed-precision defect correction vs
 plain FP64 time to a 1e-8 relative residual (2.1M-node passage, 8
-harmonics), and the batched multi-row form (three blade rows of 200k/600k/
-1.1M nodes with 2/8/4 harmonics) against per-row launches.
+harmonics), the batched multi-row form (three blade rows of 200k/600k/
+1.1M nodes with 2/8/4 harmonics) against per-row launches, five RK(5,3)
+stages with the paper's linear-solve rule, phase-lagged periodic edges on
+the measured passage, and an 8M-node passage with 16 harmonics.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnlh|reference]
 """
@@ -340,6 +342,8 @@ def run_fnlh(args):
         line["batched"] = batched_section(torch, fnlh, inputs, dev, args)
         torch.cuda.empty_cache()
         line["rk_stages"] = rk_section(torch, fnlh, inputs, dev)
+        torch.cuda.empty_cache()
+        line["periodic"] = periodic_section(torch, fnlh, inputs, dev)
         if not args.no_large:
             torch.cuda.empty_cache()
             line["large"] = large_section(torch, fnlh, inputs, dev)
@@ -390,9 +394,9 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
     return out
 
 
-def sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec, sweeps=10, reps=3):
+def sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec, sweeps=10, reps=3, sigma=None):
     """Average duration of one sweep launch (CUDA events recorded by the library around its sweep launches)."""
-    fnlh.fnlh_relax(dm, J, p.omega, B, X, 2, prec, ws)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 2, prec, ws, sigma=sigma)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     for a, z in ev:
@@ -400,7 +404,7 @@ def sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec, sweeps=10, reps=3):
         z.record()
     for a, z in ev:
         fnlh.fnlh_set_sweep_events(a, z)
-        fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec, ws)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec, ws, sigma=sigma)
     torch.cuda.synchronize()
     fnlh.fnlh_set_sweep_events(None, None)
     return sum(a.elapsed_time(z) for a, z in ev) / (reps * sweeps)
@@ -431,6 +435,42 @@ def rk_section(torch, fnlh, inputs, dev):
             out[f"{name}{'_masked' if mask else ''}"] = {
                 "seconds": time.perf_counter() - t0, "sweeps": [r["sweeps"] for r in recs],
                 "max_rel_residual": max(max(r["rel_residual"]) for r in recs)}
+    return out
+
+
+def periodic_section(torch, fnlh, inputs, dev):
+    """Phase-lagged periodic edges on the measured workload: the same passage
+    with its pitchwise boundary closed by 6,144 periodic edges, harmonic l at
+    inter-blade phase angle 2 pi l 3/8.  Sweep time per precision against the
+    same mesh without the closure, and the FP64 solve to a 1e-8 residual."""
+    c = inputs.CONFIGS[WORKLOAD]
+    out = {}
+    prep = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
+    for tag, periodic in (("plain", False), ("periodic", True)):
+        p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=WORKLOAD,
+                           periodic=periodic)
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+        J = fnlh.DeviceJacobian(dm, p.block, prep | (fnlh.FNLH_PREP_PERIODIC if periodic else 0), dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+        B = torch.from_numpy(p.b).to(dev)
+        X = torch.zeros_like(B)
+        ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev)
+        rec = {"edges": p.mesh.n_edges}
+        for name, prec in (("f64", fnlh.FNLH_F64), ("f32", fnlh.FNLH_F32), ("bf16", fnlh.FNLH_BF16)):
+            rec[f"{name}_sweep_ms"] = sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec, sigma=p.phase)
+        if periodic:
+            out["workload"] = (f"{WORKLOAD} passage closed pitchwise by {int((p.mesh.periodic != 0).sum())} "
+                               f"periodic edges, sigma_l = 2 pi l 3/8, l = 1..{p.n_harm}")
+            st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 12, 100, ws=ws,
+                                                      raise_on_error=False, flags=fnlh.FNLH_SOLVE_ZERO_GUESS,
+                                                      sigma=p.phase)
+            rec["mixed_f32_solve"] = {"status": fnlh.fnlh_strerror(st), "sweeps": sweeps,
+                                      "max_rel_residual": float(np.max(rel))}
+        out[tag] = rec
+        del dm, J, B, X, ws
+        torch.cuda.empty_cache()
+    for name in ("f64", "f32", "bf16"):
+        out[f"{name}_overhead"] = out["periodic"][f"{name}_sweep_ms"] / out["plain"][f"{name}_sweep_ms"] - 1.0
     return out
 
 

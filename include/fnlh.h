@@ -31,6 +31,14 @@
  *  - Vectors X, B, r use the real layout [n][C][b], C = 1 + 2N: column 0 is
  *    the mean flow, columns 2l-1 and 2l are Re and Im of harmonic l, whose
  *    angular frequency is omega[l-1] (the +i omega sign of Eq. phi_fft).
+ *  - Phase-lagged periodic boundaries (Eq. lhs_lin; the inter-blade phase
+ *    angle makes each harmonic's LHS different without changing its
+ *    sparsity): on a mesh with `periodic` edges, harmonic l couples node i to
+ *    the image of node j in the neighbouring blade passage, so its
+ *    off-diagonal term is J_ij e^{i s sigma[l-1]} x_j, s = +1 (next passage)
+ *    or -1 (previous) as seen from node i.  sigma (HOST [n_harm], radians,
+ *    nullable = all 0, i.e. plain periodicity) sits beside omega in every
+ *    call; J and its memory stay shared.  The mean flow carries no phase.
  *  - Blocks are row-major b x b, b = 5 (Euler) or 6 (Euler + one turbulence
  *    equation).  Off-diagonal blocks are stored in CSR order [nnz][b][b];
  *    within a row the neighbours are sorted ascending.
@@ -71,7 +79,14 @@ enum fnlh_precision {
 };
 
 /* Which derived off-diagonal copies fnlh_prepare writes (bit mask). */
-enum fnlh_prep_flags { FNLH_PREP_F64 = 1, FNLH_PREP_F32 = 2, FNLH_PREP_BF16 = 4 };
+enum fnlh_prep_flags {
+    FNLH_PREP_F64 = 1,
+    FNLH_PREP_F32 = 2,
+    FNLH_PREP_BF16 = 4,
+    /* a copy of col_idx whose top two bits carry each entry's passage
+     * offset: required by every call on a mesh with `periodic` edges */
+    FNLH_PREP_PERIODIC = 8
+};
 
 #define FNLH_MAX_HARMONICS 64
 
@@ -86,6 +101,12 @@ typedef struct fnlh_mesh {
     const int32_t *row_ptr;    /* [n+1] CSR of the symmetric neighbour graph */
     const int32_t *col_idx;    /* [2E] neighbour of each CSR entry, ascending per row */
     const int32_t *csr_edge;   /* [2E] edge of each CSR entry */
+    /* [E] nullable: passage of node j of the edge as seen from node i across a
+     * periodic boundary: +1 the next passage, -1 the previous, 0 none (an
+     * ordinary edge); other values count by their sign.  The normal of such
+     * an edge points to the image of j.  Needs a prep blob with
+     * FNLH_PREP_PERIODIC.  (Every mesh needs n_nodes < 2^30.) */
+    const int8_t *periodic;
 } fnlh_mesh;
 
 /* Jacobian construction parameters. */
@@ -122,6 +143,7 @@ typedef struct fnlh_row {
     const double *omega; /* host [n_harm] */
     const double *B;     /* [n][C][b] right-hand sides */
     double *X;           /* [n][C][b] in: x0, out: x */
+    const double *sigma; /* host [n_harm] inter-blade phase angles, or NULL */
 } fnlh_row;
 
 /* Launch shape of the batched sweep kernel (0 = library default). */
@@ -168,20 +190,24 @@ int fnlh_build_jacobian(const fnlh_mesh *mesh, const double *Q, const fnlh_param
 
 /* Derived data for the sweeps: per node an orthogonal Q_i with
  * Q_i^T (J_ii + D_i I) Q_i upper Hessenberg, and the off-diagonal blocks
- * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags.
- * Depends only on J and D, so it is independent of the number of harmonics.
+ * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags;
+ * with FNLH_PREP_PERIODIC the passage-tagged column copy (from the mesh's
+ * periodic flags; FNLH_ERR_WORKSPACE when the mesh has periodic edges and
+ * the flag is missing).  Depends only on J, D and the mesh, so it is
+ * independent of the number of harmonics and of their phase angles.
  * Call after changing offd/diag/D yourself.  Asynchronous. */
 int fnlh_prepare(const fnlh_mesh *mesh, fnlh_jacobian *J, fnlh_stream_t stream);
 
 /* `sweeps` undamped block-Jacobi sweeps ("Solution Update": block-diagonal
  * inversion point by point) on every system at once:
  *   x_i <- (J_ii + (D_i + i omega_k V_i) I)^-1 (B_i - sum_j J_ij x_j)
- * omega: HOST [n_harm].  B, X: FP64 [n][C][b]; X holds x0 on entry, the
+ * omega: HOST [n_harm]; sigma: HOST [n_harm] phase angles or NULL (see
+ * Conventions).  B, X: FP64 [n][C][b]; X holds x0 on entry, the
  * result on return.  precision selects the block copy and arithmetic of the
  * sweeps (FNLH_F64 needs FNLH_PREP_F64, etc.).  Asynchronous. */
 int fnlh_relax(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
-               const double *B, double *X, int32_t sweeps, int32_t precision, void *workspace,
-               size_t workspace_bytes, fnlh_stream_t stream);
+               const double *sigma, const double *B, double *X, int32_t sweeps, int32_t precision,
+               void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
 
 /* FP64 linear residual r_k = B_k - A_k x_k (the quantity of the paper's
  * linear-solve stopping rule, Results / Table fnlh_para) and, per system k,
@@ -190,8 +216,9 @@ int fnlh_relax(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, co
  * reduced in a fixed order, so repeated calls give identical bits.
  * Asynchronous. */
 int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
-                  const double *omega, const double *B, const double *X, double *r,
-                  double *norms, void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
+                  const double *omega, const double *sigma, const double *B, const double *X,
+                  double *r, double *norms, void *workspace, size_t workspace_bytes,
+                  fnlh_stream_t stream);
 
 /* fnlh_solve flags */
 #define FNLH_SOLVE_ZERO_GUESS 1     /* start from x0 = 0 (X is overwritten; the first residual is B) */
@@ -212,7 +239,8 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
  * max_checks checks above tol, FNLH_ERR_NONFINITE / FNLH_ERR_DIVERGED on a
  * non-finite or growing (x1e3) residual. */
 int fnlh_solve(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
-               const double *B, double *X, int32_t precision, double tol, int32_t inner_sweeps,
+               const double *sigma, const double *B, double *X, int32_t precision, double tol,
+               int32_t inner_sweeps,
                int32_t max_checks, int32_t flags, void *workspace, size_t workspace_bytes,
                int32_t *checks_done, int32_t *sweeps_done, double *rel_res, fnlh_stream_t stream);
 
@@ -246,8 +274,8 @@ size_t fnlh_batched_extra_bytes(int32_t n_rows);
  * caller.  A problem too large for the array (impossible for
  * n_harm <= FNLH_MAX_HARMONICS) returns FNLH_ERR_UNSUPPORTED. */
 int fnlh_residual_noalloc(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
-                          const double *omega, const double *B, const double *X, double *r,
-                          double *norms, fnlh_stream_t stream);
+                          const double *omega, const double *sigma, const double *B,
+                          const double *X, double *r, double *norms, fnlh_stream_t stream);
 
 /* Timing hook (not part of the paper): when both are non-NULL, every later
  * relaxation on this host thread records `begin` on its stream right before

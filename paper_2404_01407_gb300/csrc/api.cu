@@ -12,13 +12,13 @@
 namespace fnlh {
 int build_jacobian_impl(const fnlh_mesh*, const double*, const fnlh_params*, fnlh_jacobian*, cudaStream_t);
 int prepare_impl(const fnlh_mesh*, fnlh_jacobian*, cudaStream_t);
-int relax_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, double*, int, int, void*,
-               cudaStream_t);
-int solve_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, double*, int, double, int,
-               int, int, void*, int*, int*, double*, cudaStream_t);
+int relax_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, const double*, double*,
+               int, int, void*, cudaStream_t);
+int solve_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, const double*, double*, int,
+               double, int, int, int, void*, int*, int*, double*, cudaStream_t);
 int residual_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*, double*,
                     float*, const float*, int, double*, void*, cudaStream_t);
-Systems make_systems(int n_harm, const double* omega);
+Systems make_systems(int n_harm, const double* omega, const double* sigma);
 int batched_impl(const fnlh_row*, int, int, int, const fnlh_tuning*, void*, size_t, cudaStream_t);
 size_t batched_extra_bytes(int n_rows);
 void set_sweep_events(cudaEvent_t b, cudaEvent_t e);
@@ -38,6 +38,19 @@ int check_mesh(const fnlh_mesh* m, bool need_edges) {
   if (m->n_nodes > 0 && (!m->row_ptr || !m->vol)) return FNLH_ERR_ARG;
   if (m->n_edges > 0 && !m->col_idx) return FNLH_ERR_ARG;
   if (need_edges && m->n_edges > 0 && (!m->csr_edge || !m->edge_nodes || !m->normals)) return FNLH_ERR_ARG;
+  // node ids must leave the top two bits free: the kernels read them as the
+  // passage tags of periodic edges
+  if (m->n_nodes > (int32_t)kColMask) return FNLH_ERR_UNSUPPORTED;
+  return FNLH_OK;
+}
+
+// A mesh with periodic edges is only read through the prep blob's tagged
+// column copy.
+int check_periodic(const fnlh_mesh* m, const fnlh_jacobian* J) {
+  if (!m->periodic) return FNLH_OK;
+  if (!J->prep || !J->prep_ready || !(J->prep_flags & FNLH_PREP_PERIODIC)) return FNLH_ERR_WORKSPACE;
+  if (!aligned(J->prep, 256)) return FNLH_ERR_ARG;
+  if (J->prep_bytes < fnlh_prep_bytes(J->n_nodes, J->nnz, J->block, J->prep_flags)) return FNLH_ERR_WORKSPACE;
   return FNLH_OK;
 }
 
@@ -60,12 +73,12 @@ int check_prep(const fnlh_jacobian* J, int precision) {
   return FNLH_OK;
 }
 
-int check_systems(int n_harm, const double* omega) {
+int check_systems(int n_harm, const double* omega, const double* sigma) {
   if (n_harm < 0) return FNLH_ERR_ARG;
   if (n_harm > FNLH_MAX_HARMONICS) return FNLH_ERR_UNSUPPORTED;
   if (n_harm > 0 && !omega) return FNLH_ERR_ARG;
   for (int k = 0; k < n_harm; ++k)
-    if (!std::isfinite(omega[k])) return FNLH_ERR_ARG;
+    if (!std::isfinite(omega[k]) || (sigma && !std::isfinite(sigma[k]))) return FNLH_ERR_ARG;
   return FNLH_OK;
 }
 
@@ -180,56 +193,63 @@ int fnlh_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, fnlh_stream_t stream) 
   FNLH_TRY(check_jac(mesh, J));
   if (!J->prep) return FNLH_ERR_WORKSPACE;
   if (!aligned(J->prep, 256)) return FNLH_ERR_ARG;
-  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16)) return FNLH_ERR_ARG;
+  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16 | FNLH_PREP_PERIODIC)) return FNLH_ERR_ARG;
   if (J->prep_bytes < fnlh_prep_bytes(J->n_nodes, J->nnz, J->block, J->prep_flags)) return FNLH_ERR_WORKSPACE;
+  if (mesh->periodic) {
+    if (!(J->prep_flags & FNLH_PREP_PERIODIC)) return FNLH_ERR_WORKSPACE;
+    FNLH_TRY(check_mesh(mesh, true));  // the tags come from csr_edge and edge_nodes
+  }
   FNLH_TRY(prepare_impl(mesh, J, (cudaStream_t)stream));
   J->prep_ready = 1;
   return FNLH_OK;
 }
 
-int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega, const double* B,
-               double* X, int32_t sweeps, int32_t precision, void* workspace, size_t workspace_bytes,
-               fnlh_stream_t stream) {
+int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
+               const double* sigma, const double* B, double* X, int32_t sweeps, int32_t precision, void* workspace,
+               size_t workspace_bytes, fnlh_stream_t stream) {
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || sweeps < 0) return FNLH_ERR_ARG;
-  FNLH_TRY(check_systems(n_harm, omega));
+  FNLH_TRY(check_systems(n_harm, omega, sigma));
   FNLH_TRY(check_prep(J, precision));
+  FNLH_TRY(check_periodic(mesh, J));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
-  return relax_impl(mesh, J, n_harm, omega, B, X, sweeps, precision, workspace, (cudaStream_t)stream);
+  return relax_impl(mesh, J, n_harm, omega, sigma, B, X, sweeps, precision, workspace, (cudaStream_t)stream);
 }
 
 int fnlh_residual(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
-                  const double* B, const double* X, double* r, double* norms, void* workspace,
+                  const double* sigma, const double* B, const double* X, double* r, double* norms, void* workspace,
                   size_t workspace_bytes, fnlh_stream_t stream) {
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
-  FNLH_TRY(check_systems(n_harm, omega));
+  FNLH_TRY(check_systems(n_harm, omega, sigma));
+  FNLH_TRY(check_periodic(mesh, J));
   if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
   if (!workspace) return FNLH_ERR_WORKSPACE;
   if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
   const WsLayout W = ws_layout(mesh->n_nodes, J->block, n_harm, FNLH_F64);
   if (workspace_bytes < W.vec[0]) return FNLH_ERR_WORKSPACE;  // partials only
-  const Systems sys = make_systems(n_harm, omega);
+  const Systems sys = make_systems(n_harm, omega, sigma);
   return residual_launch(mesh, J, sys, B, X, r, nullptr, nullptr, 0, norms, workspace, (cudaStream_t)stream);
 }
 
-int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega, const double* B,
-               double* X, int32_t precision, double tol, int32_t inner_sweeps, int32_t max_checks, int32_t flags,
-               void* workspace, size_t workspace_bytes, int32_t* checks_done, int32_t* sweeps_done, double* rel_res,
-               fnlh_stream_t stream) {
+int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
+               const double* sigma, const double* B, double* X, int32_t precision, double tol, int32_t inner_sweeps,
+               int32_t max_checks, int32_t flags, void* workspace, size_t workspace_bytes, int32_t* checks_done,
+               int32_t* sweeps_done, double* rel_res, fnlh_stream_t stream) {
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || !(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
   if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
-  FNLH_TRY(check_systems(n_harm, omega));
+  FNLH_TRY(check_systems(n_harm, omega, sigma));
   FNLH_TRY(check_prep(J, precision));
+  FNLH_TRY(check_periodic(mesh, J));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
-  return solve_impl(mesh, J, n_harm, omega, B, X, precision, tol, inner_sweeps, max_checks, flags, workspace,
+  return solve_impl(mesh, J, n_harm, omega, sigma, B, X, precision, tol, inner_sweeps, max_checks, flags, workspace,
                     checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
 }
 
@@ -243,8 +263,9 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
     const fnlh_row& R = rows[r];
     FNLH_TRY(check_mesh(R.mesh, false));
     FNLH_TRY(check_jac(R.mesh, R.J));
-    FNLH_TRY(check_systems(R.n_harm, R.omega));
+    FNLH_TRY(check_systems(R.n_harm, R.omega, R.sigma));
     FNLH_TRY(check_prep(R.J, precision));
+    FNLH_TRY(check_periodic(R.mesh, R.J));
     if (R.mesh->n_nodes > 0 && (!R.B || !R.X)) return FNLH_ERR_ARG;
     FNLH_TRY(check_pairs(R.mesh->n_nodes, R.n_harm));
     need += ws_layout(R.mesh->n_nodes, R.J->block, R.n_harm, precision).total;
@@ -256,12 +277,14 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
 }
 
 int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
-                          const double* B, const double* X, double* r, double* norms, fnlh_stream_t stream) {
+                          const double* sigma, const double* B, const double* X, double* r, double* norms,
+                          fnlh_stream_t stream) {
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
-  FNLH_TRY(check_systems(n_harm, omega));
+  FNLH_TRY(check_systems(n_harm, omega, sigma));
+  FNLH_TRY(check_periodic(mesh, J));
   if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
-  const Systems sys = make_systems(n_harm, omega);
+  const Systems sys = make_systems(n_harm, omega, sigma);
   return residual_noalloc_launch(mesh, J, sys, B, X, r, norms, (cudaStream_t)stream);
 }
 

@@ -18,7 +18,29 @@ struct Systems {
   int32_t K;             // systems = 1 + N
   int32_t C;             // real columns = 1 + 2N
   double omega[kMaxSys]; // omega[0] = 0 (mean), omega[l] harmonic l
+  double2 phase[kMaxSys];  // (cos, sin) of the inter-blade phase angle; phase[0] = (1, 0)
 };
+
+// Column entries of a periodic mesh (the prep blob's tagged copy of col_idx)
+// carry the neighbour's blade passage in their top two bits: 1 = the next
+// passage (factor e^{+i sigma_k} on x_j), 2 = the previous one (e^{-i sigma_k}).
+constexpr uint32_t kColMask = 0x3fffffffu;
+constexpr uint32_t kSideNext = 1u, kSidePrev = 2u;
+__host__ __device__ __forceinline__ int col_of(int c) { return (int)((uint32_t)c & kColMask); }
+__host__ __device__ __forceinline__ uint32_t side_of(int c) { return (uint32_t)c >> 30; }
+
+// x <- e^{+-i sigma} x for a neighbour across the periodic boundary (side
+// kSideNext: +, kSidePrev: -), ph = (cos sigma, sin sigma).
+template <int BS, typename T>
+__device__ __forceinline__ void phase_shift(T (&re)[BS], T (&im)[BS], uint32_t side, double2 ph) {
+  const T c = (T)ph.x, s = (side == kSideNext) ? (T)ph.y : -(T)ph.y;
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    const T a = re[t], b = im[t];
+    re[t] = c * a - s * b;
+    im[t] = s * a + c * b;
+  }
+}
 
 // ------------------------------------------------------------------ loads
 
@@ -222,8 +244,9 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
 // hessf [n][b][b] f32   (when an F32/BF16 copy is requested)
 // rotf  [n][b][b] f32   Q_i in FP32 (same condition: the mixed solve's rotations)
 // offd64 / offd32 / offd16 [nnz][b][b] rotated off-diagonal copies
+// cols  [nnz] int32     col_idx with the passage tags (FNLH_PREP_PERIODIC)
 struct PrepLayout {
-  size_t rot, hess, hessf, rotf, offd64, offd32, offd16, total;
+  size_t rot, hess, hessf, rotf, offd64, offd32, offd16, cols, total;
 };
 
 inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) {
@@ -234,7 +257,7 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
   off = align256(off + (size_t)n * bb * 8);
   p.hess = off;
   off = align256(off + (size_t)n * bb * 8);
-  p.hessf = p.rotf = p.offd64 = p.offd32 = p.offd16 = (size_t)-1;
+  p.hessf = p.rotf = p.offd64 = p.offd32 = p.offd16 = p.cols = (size_t)-1;
   if (flags & (FNLH_PREP_F32 | FNLH_PREP_BF16)) {
     p.hessf = off;
     off = align256(off + (size_t)n * bb * 4);
@@ -253,11 +276,24 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
     p.offd16 = off;
     off = align256(off + (size_t)nnz * bb * 2);
   }
+  if (flags & FNLH_PREP_PERIODIC) {
+    p.cols = off;
+    off = align256(off + (size_t)nnz * 4);
+  }
   p.total = off;
   return p;
 }
 
 template <typename T> inline T* at(void* base, size_t off) { return reinterpret_cast<T*>((char*)base + off); }
+
+// The column array the sweeps and the residual read: the mesh's own, or on a
+// mesh with periodic edges the passage-tagged copy in the prep blob (the
+// entry points check that it exists before anything launches).
+inline const int32_t* csr_columns(const fnlh_mesh* m, const fnlh_jacobian* J) {
+  if (!m->periodic) return m->col_idx;
+  const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+  return at<int32_t>(J->prep, L.cols);
+}
 
 }  // namespace fnlh
 

@@ -275,6 +275,30 @@ __global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, con
     }
 }
 
+// Passage-tagged copy of col_idx (phase-lagged periodic edges), one thread
+// per row: entry p of row i across edge e gets the passage offset of its
+// neighbour as seen from i -- periodic[e] when i is the edge's first node,
+// its opposite otherwise -- in the top two bits.  No periodic array: an
+// untagged copy.
+__global__ void __launch_bounds__(128) k_tag_columns(int32_t n, const int32_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const int32_t* __restrict__ csr_edge,
+                                                     const int32_t* __restrict__ edge_nodes,
+                                                     const int8_t* __restrict__ periodic, int32_t* __restrict__ cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+    uint32_t tag = 0;
+    if (periodic) {
+      const int e = csr_edge[p];
+      int side = periodic[e] > 0 ? 1 : (periodic[e] < 0 ? -1 : 0);
+      if (edge_nodes[2 * e] != i) side = -side;
+      tag = side > 0 ? (kSideNext << 30) : (side < 0 ? (kSidePrev << 30) : 0u);
+    }
+    cols[p] = (int32_t)((uint32_t)col_idx[p] | tag);
+  }
+}
+
 template <int BS>
 int launch_build(const BuildArgs& a, cudaStream_t s) {
   if (a.n == 0) return FNLH_OK;
@@ -301,6 +325,11 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   if (J->nnz > 0 && (o64 || o32 || o16)) {
     k_rotate_offd<BS><<<(J->nnz + 127) / 128, 128, 0, s>>>(n, J->nnz, mesh->row_ptr, mesh->col_idx, J->offd, rot,
                                                          o64, o32, o16);
+    FNLH_LAUNCH_CHECK();
+  }
+  if (L.cols != (size_t)-1 && n > 0) {
+    k_tag_columns<<<(n + 127) / 128, 128, 0, s>>>(n, mesh->row_ptr, mesh->col_idx, mesh->csr_edge, mesh->edge_nodes,
+                                                  mesh->periodic, at<int32_t>(J->prep, L.cols));
     FNLH_LAUNCH_CHECK();
   }
   return FNLH_OK;

@@ -21,7 +21,7 @@ namespace fnlh {
 struct ResArgs {
   int32_t n;
   const int32_t* row_ptr;
-  const int32_t* col_idx;
+  const int32_t* col_idx;  // passage-tagged on a periodic mesh (col_of / side_of)
   const double* offd;
   const double* diag;
   const double* D;
@@ -55,14 +55,15 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
   const int p0 = a.row_ptr[i], p1 = a.x_zero ? p0 : a.row_ptr[i + 1];
   if (cplx) {
     for (int p = p0; p < p1; ++p) {
-      const int j = a.col_idx[p];
-      const double* xj = a.X + ((size_t)j * C + c0) * BS;
+      const int cj = a.col_idx[p];
+      const double* xj = a.X + ((size_t)col_of(cj) * C + c0) * BS;
       double xr[BS], xi[BS];
 #pragma unroll
       for (int t = 0; t < BS; ++t) {
         xr[t] = __ldg(xj + t);
         xi[t] = __ldg(xj + BS + t);
       }
+      if (side_of(cj)) phase_shift<BS, double>(xr, xi, side_of(cj), a.sys.phase[k]);
       const double* J = a.offd + (size_t)p * BS * BS;
 #pragma unroll
       for (int q = 0; q < BS; ++q)
@@ -75,7 +76,7 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
     }
   } else {
     for (int p = p0; p < p1; ++p) {
-      const int j = a.col_idx[p];
+      const int j = col_of(a.col_idx[p]);  // the mean flow carries no phase
       const double* xj = a.X + (size_t)j * C * BS;
       double xr[BS];
 #pragma unroll
@@ -218,7 +219,7 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   ResArgs a;
   a.n = J->n_nodes;
   a.row_ptr = m->row_ptr;
-  a.col_idx = m->col_idx;
+  a.col_idx = csr_columns(m, J);
   a.offd = J->offd;
   a.diag = J->diag;
   a.D = J->D;
@@ -287,7 +288,7 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   ResArgs a;
   a.n = J->n_nodes;
   a.row_ptr = m->row_ptr;
-  a.col_idx = m->col_idx;
+  a.col_idx = csr_columns(m, J);
   a.offd = J->offd;
   a.diag = J->diag;
   a.D = J->D;

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -35,6 +36,7 @@ struct SweepArgs {
   int32_t masked;   // 0: every system is swept; 1: only the systems set in `active`
   uint64_t active[2];
   double omega[kMaxSys];
+  double2 phase[kMaxSys];
 };
 
 // FP64: a CTA per 32 consecutive nodes, each warp taking whole systems for
@@ -43,7 +45,7 @@ template <int BS>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   if (i >= a.row.n) return;
-  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr};
+  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr, a.phase};
   const int nwarps = blockDim.x >> 5;
   for (int k = threadIdx.x >> 5; k < a.row.K; k += nwarps) {
     if (sys_active(io, k)) sweep_node_f64<BS>(a.row, io, i, k, a.x_zero != 0);
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_consta
 template <int BS, typename TJ>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_f32(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(16) float smem[];
-  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr};
+  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr, a.phase};
   sweep_tile_f32<BS, TJ>(a.row, io, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
 }
 
@@ -185,11 +187,13 @@ struct SweepOperands {
   const void* offd;
   const void* hess;
   const double* rot;
-  const float* rotf;  // FP32 basis (low-precision sweeps only)
+  const float* rotf;    // FP32 basis (low-precision sweeps only)
+  const int32_t* cols;  // column indices (passage-tagged on a periodic mesh)
 };
 
-int sweep_operands(const fnlh_jacobian* J, int precision, SweepOperands* o) {
+int sweep_operands(const fnlh_mesh* m, const fnlh_jacobian* J, int precision, SweepOperands* o) {
   const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+  o->cols = csr_columns(m, J);
   o->rot = at<double>(J->prep, L.rot);
   o->rotf = (L.rotf != (size_t)-1) ? at<float>(J->prep, L.rotf) : nullptr;
   if (precision == FNLH_F64) {
@@ -205,12 +209,18 @@ int sweep_operands(const fnlh_jacobian* J, int precision, SweepOperands* o) {
   return FNLH_OK;
 }
 
-Systems make_systems(int n_harm, const double* omega) {
+Systems make_systems(int n_harm, const double* omega, const double* sigma) {
   Systems s;
   s.K = 1 + n_harm;
   s.C = 1 + 2 * n_harm;
-  for (int k = 0; k < kMaxSys; ++k) s.omega[k] = 0.0;
-  for (int k = 1; k <= n_harm; ++k) s.omega[k] = omega[k - 1];
+  for (int k = 0; k < kMaxSys; ++k) {
+    s.omega[k] = 0.0;
+    s.phase[k] = make_double2(1.0, 0.0);
+  }
+  for (int k = 1; k <= n_harm; ++k) {
+    s.omega[k] = omega[k - 1];
+    if (sigma) s.phase[k] = make_double2(std::cos(sigma[k - 1]), std::sin(sigma[k - 1]));
+  }
   return s;
 }
 
@@ -267,7 +277,7 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.row.K = sys.K;
   a.row.divK = make_fastdiv((uint32_t)sys.K);
   a.row.row_ptr = m->row_ptr;
-  a.row.col_idx = m->col_idx;
+  a.row.col_idx = op.cols;
   a.row.offd = op.offd;
   a.row.hess = op.hess;
   a.row.vol = m->vol;
@@ -276,7 +286,10 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.masked = active ? 1 : 0;
   a.active[0] = active ? active[0] : ~0ull;
   a.active[1] = active ? active[1] : ~0ull;
-  for (int k = 0; k < kMaxSys; ++k) a.omega[k] = sys.omega[k];
+  for (int k = 0; k < kMaxSys; ++k) {
+    a.omega[k] = sys.omega[k];
+    a.phase[k] = sys.phase[k];
+  }
   size_t smem = 0;
   int rc = FNLH_OK;
   if constexpr (sizeof(T) == 4) {
@@ -300,12 +313,12 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
 }
 
 template <int BS, typename TJ, typename T>
-int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-                double* X, int sweeps, int precision, void* ws, cudaStream_t s) {
+int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
+                const double* B, double* X, int sweeps, int precision, void* ws, cudaStream_t s) {
   SweepOperands op;
-  int rc = sweep_operands(J, precision, &op);
+  int rc = sweep_operands(m, J, precision, &op);
   if (rc) return rc;
-  const Systems sys = make_systems(n_harm, omega);
+  const Systems sys = make_systems(n_harm, omega, sigma);
   const WsLayout W = ws_layout(J->n_nodes, BS, n_harm, precision);
   T* bt = at<T>(ws, W.vec[0]);
   T* x0 = at<T>(ws, W.vec[1]);
@@ -319,16 +332,18 @@ int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   return rotate_out<BS, T>(n, sys.K, op.rot, res, X, 0, s);
 }
 
-int relax_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-               double* X, int sweeps, int precision, void* ws, cudaStream_t s) {
+int relax_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
+               const double* B, double* X, int sweeps, int precision, void* ws, cudaStream_t s) {
+#define FNLH_RELAX(BS, TJ, T) relax_typed<BS, TJ, T>(m, J, n_harm, omega, sigma, B, X, sweeps, precision, ws, s)
   if (J->block == 5) {
-    if (precision == FNLH_F64) return relax_typed<5, double, double>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
-    if (precision == FNLH_F32) return relax_typed<5, float, float>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
-    return relax_typed<5, __nv_bfloat16, float>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
+    if (precision == FNLH_F64) return FNLH_RELAX(5, double, double);
+    if (precision == FNLH_F32) return FNLH_RELAX(5, float, float);
+    return FNLH_RELAX(5, __nv_bfloat16, float);
   }
-  if (precision == FNLH_F64) return relax_typed<6, double, double>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
-  if (precision == FNLH_F32) return relax_typed<6, float, float>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
-  return relax_typed<6, __nv_bfloat16, float>(m, J, n_harm, omega, B, X, sweeps, precision, ws, s);
+  if (precision == FNLH_F64) return FNLH_RELAX(6, double, double);
+  if (precision == FNLH_F32) return FNLH_RELAX(6, float, float);
+  return FNLH_RELAX(6, __nv_bfloat16, float);
+#undef FNLH_RELAX
 }
 
 // ------------------------------------------------------------------ solve
@@ -360,13 +375,13 @@ static int check_norms(const double* hn, int K, double tol, Check* ck, bool firs
 }
 
 template <int BS, typename TJ, typename T>
-int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-                double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
+int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
+                const double* B, double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
                 int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
   SweepOperands op;
-  int rc = sweep_operands(J, precision, &op);
+  int rc = sweep_operands(m, J, precision, &op);
   if (rc) return rc;
-  const Systems sys = make_systems(n_harm, omega);
+  const Systems sys = make_systems(n_harm, omega, sigma);
   const WsLayout W = ws_layout(J->n_nodes, BS, n_harm, precision);
   const int n = J->n_nodes, K = sys.K;
   double* norms = at<double>(ws, W.norms);
@@ -435,12 +450,12 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   return conv ? FNLH_OK : FNLH_ERR_NOT_CONVERGED;
 }
 
-int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* B,
-               double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
+int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
+               const double* B, double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
                int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
-#define FNLH_SOLVE(BS, TJ, T)                                                                                  \
-  solve_typed<BS, TJ, T>(m, J, n_harm, omega, B, X, precision, tol, inner, max_checks, flags, ws, checks_done, \
-                         sweeps_done, rel_res, s)
+#define FNLH_SOLVE(BS, TJ, T)                                                                                   \
+  solve_typed<BS, TJ, T>(m, J, n_harm, omega, sigma, B, X, precision, tol, inner, max_checks, flags, ws,       \
+                         checks_done, sweeps_done, rel_res, s)
   if (J->block == 5) {
     if (precision == FNLH_F64) return FNLH_SOLVE(5, double, double);
     if (precision == FNLH_F32) return FNLH_SOLVE(5, float, float);
@@ -470,6 +485,7 @@ struct BatchRow {
   void* x[2];        // ping-pong iterate buffers
   long long tile0;   // first global tile of this row
   double omega[kMaxSys];
+  double2 phase[kMaxSys];
 };
 
 struct BatchArgs {
@@ -485,7 +501,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched(const __grid
     int r = 0;
     while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
     const BatchRow& D = a.row[r];
-    const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, nullptr};
+    const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, nullptr, D.phase};
     const long long g0 = (t - D.tile0) * blockDim.x;
     if constexpr (sizeof(T) == 8) {
       const long long g = g0 + threadIdx.x;
@@ -516,9 +532,9 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   SweepOperands ops[kMaxBatchRows];
   for (int r = 0; r < n_rows; ++r) {
     const fnlh_row& R = rows[r];
-    int rc = sweep_operands(R.J, precision, &ops[r]);
+    int rc = sweep_operands(R.mesh, R.J, precision, &ops[r]);
     if (rc) return rc;
-    const Systems sys = make_systems(R.n_harm, R.omega);
+    const Systems sys = make_systems(R.n_harm, R.omega, R.sigma);
     const WsLayout W = ws_layout(R.mesh->n_nodes, BS, R.n_harm, precision);
     char* base = (char*)ws + off;
     off += W.total;
@@ -527,7 +543,7 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
     D.row.K = sys.K;
     D.row.divK = make_fastdiv((uint32_t)sys.K);
     D.row.row_ptr = R.mesh->row_ptr;
-    D.row.col_idx = R.mesh->col_idx;
+    D.row.col_idx = ops[r].cols;
     D.row.offd = ops[r].offd;
     D.row.hess = ops[r].hess;
     D.row.vol = R.mesh->vol;
@@ -537,7 +553,10 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
     D.tile0 = tiles;
     tiles += ((long long)D.row.n * D.row.K + threads - 1) / threads;
     kmin = std::min(kmin, sys.K);
-    for (int k = 0; k < kMaxSys; ++k) D.omega[k] = sys.omega[k];
+    for (int k = 0; k < kMaxSys; ++k) {
+      D.omega[k] = sys.omega[k];
+      D.phase[k] = sys.phase[k];
+    }
     if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.B, (T*)D.row.Bt, s))) return rc;
     if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.X, (T*)D.x[0], s))) return rc;
   }

@@ -208,7 +208,7 @@ struct TileRow {
   int32_t n, K;
   FastDiv divK;      // division by K (pair index -> node), n K < 2^31
   const int32_t* row_ptr;
-  const int32_t* col_idx;
+  const int32_t* col_idx;  // possibly passage-tagged (col_of / side_of)
   const void* offd;  // rotated off-diagonal blocks (TJ)
   const void* hess;  // [n][b][b] (double for FP64 sweeps, float otherwise)
   const double* vol;
@@ -222,6 +222,7 @@ struct SweepIO {
   void* Xout;            // [n][K][b] complex
   const double* omega;   // [K], omega[0] = 0
   const uint64_t* active;  // bit k set: system k is swept; null: every system
+  const double2* phase;  // [K] (cos, sin) of the inter-blade phase angles, phase[0] = (1, 0)
 };
 
 __device__ __forceinline__ bool sys_active(const SweepIO& io, int k) {
@@ -260,9 +261,10 @@ __device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& 
     const double* __restrict__ offd = (const double*)R.offd;
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
-      const int j = __ldg(R.col_idx + p);
+      const int cj = __ldg(R.col_idx + p);
       Cvec<BS, double> x;
-      load_slice<BS>(X + ((size_t)j * R.K + k) * 2 * BS, x);
+      load_slice<BS>(X + ((size_t)col_of(cj) * R.K + k) * 2 * BS, x);
+      if (side_of(cj)) phase_shift<BS, double>(x.re, x.im, side_of(cj), io.phase[k]);
       double J[BS * BS];
       load_block<BS>(offd + (size_t)p * BS * BS, J);
 #pragma unroll
@@ -297,7 +299,7 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
     const double* __restrict__ offd = (const double*)R.offd;
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
-      const int j = __ldg(R.col_idx + p);
+      const int j = col_of(__ldg(R.col_idx + p));  // the mean flow carries no phase
       const double* xs = X + (size_t)j * R.K * 2 * BS;
       double xr[BS];
 #pragma unroll
@@ -412,16 +414,21 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
       // software pipeline: the next neighbour's slice is in flight while the
       // current one is multiplied
       Cvec<BS, float> xn;
+      uint32_t side_n = 0;
       if (p0 < p1) {
-        const int j = staged ? sC[p0 - p_first] : __ldg(R.col_idx + p0);
-        load_slice<BS>(Xk + (size_t)j * stride, xn);
+        const int cj = staged ? sC[p0 - p_first] : __ldg(R.col_idx + p0);
+        side_n = side_of(cj);
+        load_slice<BS>(Xk + (size_t)col_of(cj) * stride, xn);
       }
       for (int p = p0; p < p1; ++p) {
-        const Cvec<BS, float> x = xn;
+        Cvec<BS, float> x = xn;
+        const uint32_t side = side_n;
         if (p + 1 < p1) {
-          const int j = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
-          load_slice<BS>(Xk + (size_t)j * stride, xn);
+          const int cj = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
+          side_n = side_of(cj);
+          load_slice<BS>(Xk + (size_t)col_of(cj) * stride, xn);
         }
+        if (side) phase_shift<BS, float>(x.re, x.im, side, io.phase[k]);
         if (staged) {
           spmv_rows_smem<BS>(sJ + (size_t)(p - p_first) * BS * BS, x, s);
         } else {

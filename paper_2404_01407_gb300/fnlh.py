@@ -36,7 +36,7 @@ FNLH_ERR_NOT_CONVERGED = -8
 FNLH_ERR_BAD_MESH = -9
 
 FNLH_F64, FNLH_F32, FNLH_BF16 = 0, 1, 2
-FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16 = 1, 2, 4
+FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16, FNLH_PREP_PERIODIC = 1, 2, 4, 8
 PRECISIONS = {"f64": FNLH_F64, "f32": FNLH_F32, "bf16": FNLH_BF16}
 PREP_FOR = {FNLH_F64: FNLH_PREP_F64, FNLH_F32: FNLH_PREP_F32, FNLH_BF16: FNLH_PREP_BF16}
 MAX_HARMONICS = 64
@@ -44,7 +44,7 @@ MAX_HARMONICS = 64
 
 class fnlh_mesh(ctypes.Structure):
     _fields_ = [("n_nodes", c_i32), ("n_edges", c_i32), ("edge_nodes", c_vp), ("normals", c_vp),
-                ("vol", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("csr_edge", c_vp)]
+                ("vol", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("csr_edge", c_vp), ("periodic", c_vp)]
 
 
 class fnlh_params(ctypes.Structure):
@@ -60,7 +60,8 @@ class fnlh_jacobian(ctypes.Structure):
 
 class fnlh_row(ctypes.Structure):
     _fields_ = [("mesh", ctypes.POINTER(fnlh_mesh)), ("J", ctypes.POINTER(fnlh_jacobian)),
-                ("n_harm", c_i32), ("omega", ctypes.POINTER(c_f64)), ("B", c_vp), ("X", c_vp)]
+                ("n_harm", c_i32), ("omega", ctypes.POINTER(c_f64)), ("B", c_vp), ("X", c_vp),
+                ("sigma", ctypes.POINTER(c_f64))]
 
 
 class fnlh_tuning(ctypes.Structure):
@@ -87,18 +88,22 @@ _SIGS = {
                                            ctypes.POINTER(fnlh_jacobian), c_vp]),
     "fnlh_prepare": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_vp]),
     "fnlh_relax": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
-                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_i32, c_vp, c_sz, c_vp]),
+                                  ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_i32, c_vp, c_sz,
+                                  c_vp]),
     "fnlh_residual": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
-                                     ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+                                     ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp, c_sz,
+                                     c_vp]),
     "fnlh_solve": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
-                                  ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_f64, c_i32, c_i32, c_i32, c_vp, c_sz,
+                                  ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp, c_vp, c_i32, c_f64, c_i32, c_i32,
+                                  c_i32, c_vp, c_sz,
                                   ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_f64), c_vp]),
     "fnlh_relax_batched": (ctypes.c_int, [ctypes.POINTER(fnlh_row), c_i32, c_i32, c_i32,
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
     "fnlh_batched_extra_bytes": (c_sz, [c_i32]),
     "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
     "fnlh_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
-                                             ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp, c_vp]),
+                                             ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp,
+                                             c_vp]),
 }
 
 
@@ -157,12 +162,25 @@ def _omega(omega):
     return arr, arr.ctypes.data_as(ctypes.POINTER(c_f64))
 
 
+def _sigma(sigma, n_harm):
+    """Host phase-angle array (kept alive by the caller) and its pointer, or
+    (None, None) for plain periodicity."""
+    if sigma is None:
+        return None, None
+    arr = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
+    if arr.shape[0] != n_harm:
+        raise ValueError("sigma needs one phase angle per harmonic")
+    if arr.size == 0:
+        return None, None
+    return arr, arr.ctypes.data_as(ctypes.POINTER(c_f64))
+
+
 # ------------------------------------------------------------------ objects
 
 class DeviceMesh:
     """Mesh arrays on the device plus the ctypes fnlh_mesh describing them."""
 
-    def __init__(self, n_nodes, edge_nodes, normals, vol, device="cuda"):
+    def __init__(self, n_nodes, edge_nodes, normals, vol, device="cuda", periodic=None):
         en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
         n_edges = en.shape[0]
         row_ptr = np.zeros(n_nodes + 1, dtype=np.int32)
@@ -178,12 +196,17 @@ class DeviceMesh:
         self.row_ptr = torch.from_numpy(row_ptr).to(dev)
         self.col_idx = torch.from_numpy(col_idx[: 2 * n_edges].copy()).to(dev)
         self.csr_edge = torch.from_numpy(csr_edge[: 2 * n_edges].copy()).to(dev)
+        self.periodic = None
+        if periodic is not None:
+            per = np.ascontiguousarray(periodic, dtype=np.int8).reshape(n_edges)
+            self.periodic = torch.from_numpy(per).to(dev) if n_edges else None
         self.c = fnlh_mesh(self.n_nodes, self.n_edges, _ptr(self.edge_nodes), _ptr(self.normals), _ptr(self.vol),
-                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.csr_edge))
+                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.csr_edge), _ptr(self.periodic))
 
     @classmethod
     def from_mesh(cls, mesh, device="cuda"):
-        return cls(mesh.n_nodes, mesh.edge_nodes, mesh.normals, mesh.vol, device)
+        return cls(mesh.n_nodes, mesh.edge_nodes, mesh.normals, mesh.vol, device,
+                   periodic=getattr(mesh, "periodic", None))
 
 
 class DeviceJacobian:
@@ -250,26 +273,28 @@ def fnlh_prepare(dmesh: DeviceMesh, J: DeviceJacobian, stream=None):
     _check(lib().fnlh_prepare(ctypes.byref(dmesh.c), ctypes.byref(J.c), _stream(stream)), "fnlh_prepare")
 
 
-def fnlh_relax(dmesh, J, omega, B, X, sweeps, precision=FNLH_F64, ws=None, stream=None):
+def fnlh_relax(dmesh, J, omega, B, X, sweeps, precision=FNLH_F64, ws=None, stream=None, sigma=None):
     om, omp = _omega(omega)
     n_harm = len(np.atleast_1d(omega))
+    sg, sgp = _sigma(sigma, n_harm)
     if ws is None:
         ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
-    st = lib().fnlh_relax(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), int(sweeps),
+    st = lib().fnlh_relax(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, sgp, _ptr(B), _ptr(X), int(sweeps),
                           int(precision), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fnlh_relax")
 
 
-def fnlh_residual(dmesh, J, omega, B, X, r=None, norms=None, ws=None, stream=None):
+def fnlh_residual(dmesh, J, omega, B, X, r=None, norms=None, ws=None, stream=None, sigma=None):
     """Returns the device tensor of norms [K, 2] = (||r_k||^2, ||B_k||^2)."""
     om, omp = _omega(omega)
     n_harm = len(np.atleast_1d(omega))
+    sg, sgp = _sigma(sigma, n_harm)
     K = 1 + n_harm
     if norms is None:
         norms = torch.empty((K, 2), dtype=torch.float64, device=B.device)
     if ws is None:
         ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
-    st = lib().fnlh_residual(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), _ptr(r),
+    st = lib().fnlh_residual(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, sgp, _ptr(B), _ptr(X), _ptr(r),
                              _ptr(norms), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fnlh_residual")
     return norms
@@ -280,15 +305,16 @@ FNLH_SOLVE_MASK_CONVERGED = 2
 
 
 def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, ws=None, stream=None,
-               raise_on_error=True, flags=0):
+               raise_on_error=True, flags=0, sigma=None):
     """Returns (status, checks_done, sweeps_done, rel_res[K])."""
     om, omp = _omega(omega)
     n_harm = len(np.atleast_1d(omega))
+    sg, sgp = _sigma(sigma, n_harm)
     if ws is None:
         ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
     checks, sweeps = c_i32(0), c_i32(0)
     rel = (c_f64 * (1 + n_harm))()
-    st = lib().fnlh_solve(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X), int(precision),
+    st = lib().fnlh_solve(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, sgp, _ptr(B), _ptr(X), int(precision),
                           float(tol), int(inner_sweeps), int(max_checks), int(flags), _ptr(ws), ws.numel(),
                           ctypes.byref(checks),
                           ctypes.byref(sweeps), rel, _stream(stream))
@@ -301,14 +327,19 @@ class BatchedRows:
     """Holds the ctypes row array (and the omega buffers it points to)."""
 
     def __init__(self, rows):
-        # rows: list of (dmesh, J, omega, B, X)
+        # rows: list of (dmesh, J, omega, B, X) or (dmesh, J, omega, B, X, sigma)
         self.keep = []
+        self.sigmas = []
         arr = (fnlh_row * len(rows))()
-        for r, (dm, J, omega, B, X) in enumerate(rows):
+        for r, row in enumerate(rows):
+            dm, J, omega, B, X = row[:5]
+            sigma = row[5] if len(row) > 5 else None
             om, omp = _omega(omega)
+            sg, sgp = _sigma(sigma, len(np.atleast_1d(omega)))
             self.keep.append((dm, J, om, B, X))
+            self.sigmas.append(sg)
             arr[r] = fnlh_row(ctypes.pointer(dm.c), ctypes.pointer(J.c), len(np.atleast_1d(omega)), omp,
-                              _ptr(B), _ptr(X))
+                              _ptr(B), _ptr(X), sgp)
         self.arr = arr
         self.n = len(rows)
 
@@ -333,16 +364,17 @@ def fnlh_set_sweep_events(begin=None, end=None):
     _check(lib().fnlh_set_sweep_events(b, e), "fnlh_set_sweep_events")
 
 
-def fnlh_residual_noalloc(dmesh, J, omega, B, X, r=None, norms=None, stream=None):
+def fnlh_residual_noalloc(dmesh, J, omega, B, X, r=None, norms=None, stream=None, sigma=None):
     """fnlh_residual without a workspace: for callers that cannot allocate
     device memory (the library keeps the partial sums in its own static device
     array).  `norms` must be given by such a caller; it is allocated here only
     as a convenience when omitted."""
     om, omp = _omega(omega)
     n_harm = len(np.atleast_1d(omega))
+    sg, sgp = _sigma(sigma, n_harm)
     if norms is None:
         norms = torch.empty((1 + n_harm, 2), dtype=torch.float64, device=B.device)
-    st = lib().fnlh_residual_noalloc(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, _ptr(B), _ptr(X),
+    st = lib().fnlh_residual_noalloc(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, sgp, _ptr(B), _ptr(X),
                                      _ptr(r), _ptr(norms), _stream(stream))
     _check(st, "fnlh_residual_noalloc")
     return norms

@@ -35,17 +35,18 @@ EPS = 0.6
 
 
 def stage_solve(dmesh, J, omega, B_scaled, X, precision=fnlh.FNLH_F64, tol=LINEAR_TOL,
-                max_iterations=LINEAR_MAX_ITERATIONS, sweeps_per_check=2, mask=True, ws=None):
-    """One stage's inexact solve K x = B' from x0 = 0 with the paper's rule.
+                max_iterations=LINEAR_MAX_ITERATIONS, sweeps_per_check=2, mask=True, ws=None, sigma=None):
+    """One stage's inexact solve K x = B' from x0 = 0 with the paper's rule
+    (sigma: inter-blade phase angles on a mesh with periodic edges).
     Returns (status, checks, sweeps, rel[K])."""
     checks = max_iterations // sweeps_per_check + 1
     flags = fnlh.FNLH_SOLVE_ZERO_GUESS | (fnlh.FNLH_SOLVE_MASK_CONVERGED if mask else 0)
     return fnlh.fnlh_solve(dmesh, J, omega, B_scaled, X, precision, tol, sweeps_per_check, checks, ws=ws,
-                           raise_on_error=False, flags=flags)
+                           raise_on_error=False, flags=flags, sigma=sigma)
 
 
 def run_stages(dmesh, J, omega, stage_residuals, precision=fnlh.FNLH_F64, eps=EPS, mask=True,
-               sweeps_per_check=2, ws=None):
+               sweeps_per_check=2, ws=None, sigma=None):
     """Five stages: for stage k, B' = -(Gamma alpha_k) R^(k), Delta Q^(k) = K^-1 B'.
     stage_residuals: five device tensors [n][C][b] (R^(k), real layout).
     Returns the list of Delta Q^(k) tensors and per-stage records."""
@@ -56,7 +57,7 @@ def run_stages(dmesh, J, omega, stage_residuals, precision=fnlh.FNLH_F64, eps=EP
         B = R * scale
         X = B.new_empty(B.shape)
         st, checks, sweeps, rel = stage_solve(dmesh, J, omega, B, X, precision, mask=mask,
-                                              sweeps_per_check=sweeps_per_check, ws=ws)
+                                              sweeps_per_check=sweeps_per_check, ws=ws, sigma=sigma)
         if st not in (fnlh.FNLH_OK, fnlh.FNLH_ERR_NOT_CONVERGED):
             raise fnlh.FnlhError(st, f"RK stage {k + 1}")
         updates.append(X)

@@ -81,7 +81,7 @@ def test_sizes_independent_of_harmonics():
 def test_validation_rejects_before_launch():
     L = fnlh.lib()
     null = ctypes.POINTER(fnlh.fnlh_mesh)()
-    assert L.fnlh_relax(null, None, 0, None, None, None, 1, 0, None, 0, None) == fnlh.FNLH_ERR_ARG
+    assert L.fnlh_relax(null, None, 0, None, None, None, None, 1, 0, None, 0, None) == fnlh.FNLH_ERR_ARG
     m = fnlh.fnlh_mesh(4, 0, None, None, None, None, None, None)
     assert L.fnlh_prepare(ctypes.byref(m), None, None) == fnlh.FNLH_ERR_ARG
     J = fnlh.fnlh_jacobian(4, 0, 7, None, None, None, None, 0, 0, 0)
@@ -90,14 +90,47 @@ def test_validation_rejects_before_launch():
     J5 = fnlh.fnlh_jacobian(4, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
     # no prep blob -> workspace error; bad precision -> arg error; too many harmonics -> unsupported
     om = (ctypes.c_double * 70)()
-    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, 1, 0, None, 0, None) \
+    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, None, 1, 0, None, 0, None) \
         == fnlh.FNLH_ERR_WORKSPACE
-    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, 1, 9, None, 0, None) \
+    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, None, 1, 9, None, 0, None) \
         == fnlh.FNLH_ERR_ARG
-    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 65, om, None, None, 1, 0, None, 0, None) \
+    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 65, om, None, None, None, 1, 0, None, 0, None) \
         == fnlh.FNLH_ERR_UNSUPPORTED
-    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, -1, 0, None, 0, None) \
+    assert L.fnlh_relax(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, None, -1, 0, None, 0, None) \
         == fnlh.FNLH_ERR_ARG
     om[0] = float("nan")
-    assert L.fnlh_residual(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, None, None, None, 0, None) \
+    assert L.fnlh_residual(ctypes.byref(m2), ctypes.byref(J5), 1, om, None, None, None, None, None, None, 0, None) \
         == fnlh.FNLH_ERR_ARG
+
+
+def test_periodic_validation_rejects_before_launch():
+    """Phase-lagged periodic edges: the tagged column copy must be in the prep
+    blob, node ids must leave the top two bits free, phase angles finite."""
+    L = fnlh.lib()
+    per = ctypes.c_void_p(4096)  # never dereferenced: validation fails first
+    vol = ctypes.c_void_p(256)
+    m = fnlh.fnlh_mesh(4, 0, None, None, vol, vol, None, None, per)
+    J5 = fnlh.fnlh_jacobian(4, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
+    om = (ctypes.c_double * 2)(1.0, 2.0)
+    sig = (ctypes.c_double * 2)(0.5, float("nan"))
+    # no prep at all, then a prepared blob without the periodic copy
+    assert L.fnlh_residual(ctypes.byref(m), ctypes.byref(J5), 1, om, None, vol, vol, None, vol, vol, 1 << 20,
+                           None) == fnlh.FNLH_ERR_WORKSPACE
+    nb = fnlh.fnlh_prep_bytes(4, 0, 5, fnlh.FNLH_PREP_F64)
+    Jp = fnlh.fnlh_jacobian(4, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), ctypes.c_void_p(1 << 12), nb,
+                            fnlh.FNLH_PREP_F64, 1)
+    assert L.fnlh_relax(ctypes.byref(m), ctypes.byref(Jp), 1, om, None, vol, vol, 1, 0, vol, 1 << 20, None) \
+        == fnlh.FNLH_ERR_WORKSPACE
+    assert L.fnlh_prepare(ctypes.byref(m), ctypes.byref(Jp), None) == fnlh.FNLH_ERR_WORKSPACE
+    # a non-finite phase angle
+    assert L.fnlh_relax(ctypes.byref(m), ctypes.byref(J5), 2, om, sig, vol, vol, 1, 0, vol, 1 << 20, None) \
+        == fnlh.FNLH_ERR_ARG
+    # node ids above 2^30 - 1 cannot leave room for the passage tags (any mesh)
+    big = fnlh.fnlh_mesh(1 << 30, 0, None, None, vol, vol, None, None, None)
+    Jb = fnlh.fnlh_jacobian(1 << 30, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
+    assert L.fnlh_residual(ctypes.byref(big), ctypes.byref(Jb), 0, om, None, vol, vol, None, vol, vol, 1 << 20,
+                           None) == fnlh.FNLH_ERR_UNSUPPORTED
+    # the tagged copy adds nnz int32 (256-aligned) to the blob
+    n, nnz = 1000, 6000
+    assert fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_PERIODIC) == \
+        fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64) + ((nnz * 4 + 255) // 256) * 256

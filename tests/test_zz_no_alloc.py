@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 def _call_noalloc(dm, J, omega, B, X, r, norms):
     om = np.ascontiguousarray(np.atleast_1d(np.asarray(omega, dtype=np.float64)))
     omp = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    st = fnlh.lib().fnlh_residual_noalloc(ctypes.byref(dm.c), ctypes.byref(J.c), len(om), omp,
+    st = fnlh.lib().fnlh_residual_noalloc(ctypes.byref(dm.c), ctypes.byref(J.c), len(om), omp, None,
                                           ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
                                           ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(norms.data_ptr()),
                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
