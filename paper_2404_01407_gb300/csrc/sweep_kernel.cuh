@@ -196,6 +196,11 @@ __device__ __forceinline__ void stage_i32(int* __restrict__ dst, const int* __re
 // Shared-memory floats needed by a staged tile of `threads` pairs: the
 // tile's blocks, factors and neighbour indices.
 __host__ __device__ inline int stage_cap_nodes(int threads, int K) { return (threads + K - 1) / K + 1; }
+// Staging pays when a staged block serves enough threads: a node's blocks are
+// read by its K threads, and below this K the stage's shared memory costs
+// more occupancy than the reuse wins (measured on GB300: K = 3..5 run 5-27%
+// faster unstaged, K = 7 and up 12-15% faster staged).
+constexpr int kStageMinSystems = 6;
 constexpr int kStageDegree = 7;  // blocks per node the stage buffer is sized for (hex meshes: <= 6)
 __host__ __device__ inline int stage_floats(int threads, int K, int BS) {
   const int nodes = stage_cap_nodes(threads, K);
@@ -207,6 +212,7 @@ __host__ __device__ inline int stage_floats(int threads, int K, int BS) {
 struct TileRow {
   int32_t n, K;
   FastDiv divK;      // division by K (pair index -> node), n K < 2^31
+  int32_t stage;     // 1: stage the tile's blocks in shared memory when they fit
   const int32_t* row_ptr;
   const int32_t* col_idx;  // possibly passage-tagged (col_of / side_of)
   const void* offd;  // rotated off-diagonal blocks (TJ)
@@ -368,6 +374,43 @@ __device__ __forceinline__ void spmv_rows_smem(const float* jb, const Cvec<BS, f
   }
 }
 
+// s -= J x for one block read straight from global memory, row by row with
+// vector loads (a row of an FP32 block starts on 8 bytes, of a BF16 block on
+// 4 bytes, for even BS); the node's K threads share the block through L1.
+template <int BS, typename TJ>
+__device__ __forceinline__ void spmv_rows_global(const TJ* __restrict__ jb, const Cvec<BS, float>& x,
+                                                 Cvec<BS, float>& s) {
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    float jr[BS];
+    if constexpr (BS % 2 == 0 && sizeof(TJ) == 2) {
+      const uint32_t* q = reinterpret_cast<const uint32_t*>(jb + r * BS);
+#pragma unroll
+      for (int t = 0; t < BS / 2; ++t) {
+        const uint32_t w = __ldg(q + t);
+        jr[2 * t] = bf16_lo(w);
+        jr[2 * t + 1] = bf16_hi(w);
+      }
+    } else if constexpr (BS % 2 == 0) {
+      const float2* q = reinterpret_cast<const float2*>(jb + r * BS);
+#pragma unroll
+      for (int t = 0; t < BS / 2; ++t) {
+        const float2 f = __ldg(q + t);
+        jr[2 * t] = f.x;
+        jr[2 * t + 1] = f.y;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < BS; ++t) jr[t] = ld<float, TJ>(jb + r * BS + t);
+    }
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      s.re[r] -= jr[t] * x.re[t];
+      s.im[r] -= jr[t] * x.im[t];
+    }
+  }
+}
+
 // Every thread of the CTA must call this (it synchronises).
 template <int BS, typename TJ>
 __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& io, long long g0, bool x_zero,
@@ -382,7 +425,7 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
   const int p_first = __ldg(R.row_ptr + i_first), p_end = __ldg(R.row_ptr + i_last + 1);
   const int nblk = x_zero ? 0 : (p_end - p_first);
   // blocks, factors and neighbour indices of the tile (uniform over the CTA)
-  const bool staged = (nblk + nodes) * BS * BS + nblk <= smem_floats;
+  const bool staged = R.stage && (nblk + nodes) * BS * BS + nblk <= smem_floats;
   float* sJ = smem;
   float* sH = smem + nblk * BS * BS;
   int* sC = reinterpret_cast<int*>(sH + nodes * BS * BS);
@@ -429,27 +472,8 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
           load_slice<BS>(Xk + (size_t)col_of(cj) * stride, xn);
         }
         if (side) phase_shift<BS, float>(x.re, x.im, side, io.phase[k]);
-        if (staged) {
-          spmv_rows_smem<BS>(sJ + (size_t)(p - p_first) * BS * BS, x, s);
-        } else {
-          float J[BS * BS];
-          if constexpr (sizeof(TJ) == 2) {
-            const uint16_t* q = reinterpret_cast<const uint16_t*>(R.offd) + (size_t)p * BS * BS;
-#pragma unroll
-            for (int e = 0; e < BS * BS; ++e) J[e] = __uint_as_float((uint32_t)__ldg(q + e) << 16);
-          } else {
-            const float* q = (const float*)R.offd + (size_t)p * BS * BS;
-#pragma unroll
-            for (int e = 0; e < BS * BS; ++e) J[e] = __ldg(q + e);
-          }
-#pragma unroll
-          for (int r = 0; r < BS; ++r)
-#pragma unroll
-            for (int t = 0; t < BS; ++t) {
-              s.re[r] -= J[r * BS + t] * x.re[t];
-              s.im[r] -= J[r * BS + t] * x.im[t];
-            }
-        }
+        if (staged) spmv_rows_smem<BS>(sJ + (size_t)(p - p_first) * BS * BS, x, s);
+        else spmv_rows_global<BS, TJ>((const TJ*)R.offd + (size_t)p * BS * BS, x, s);
       }
     }
     const float* H = staged ? sH + (size_t)(i - i_first) * BS * BS : (const float*)R.hess + (size_t)i * BS * BS;
