@@ -84,7 +84,7 @@ def _bind(lib):
     # n, b, n_harm, row_ptr, col_idx, offd, diag, D, vol, omega, side, sigma, B
     common = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p,
               _f64p, _f64p, ctypes.c_void_p, ctypes.c_void_p, _f64p]
-    lib.oracle_jacobi.argtypes = common + [_f64p, ctypes.c_int]
+    lib.oracle_jacobi.argtypes = common + [_f64p, ctypes.c_int, ctypes.c_void_p]
     lib.oracle_jacobi.restype = ctypes.c_int
     lib.oracle_residual.argtypes = common + [_f64p, ctypes.c_void_p, _f64p]
     lib.oracle_residual.restype = ctypes.c_int
@@ -215,13 +215,20 @@ def _sys_args(jac: Jacobian, vol, omega, sigma, keep):
             _f64(np.atleast_1d(omega)) if len(omega) else np.zeros(1), side_p, sigma_p)
 
 
-def jacobi(jac: Jacobian, vol, omega, B, sweeps: int, X0=None, sigma=None) -> np.ndarray:
+def jacobi(jac: Jacobian, vol, omega, B, sweeps: int, X0=None, sigma=None, part=None) -> np.ndarray:
     """x after `sweeps` undamped block-Jacobi sweeps from X0 (zero if None);
-    sigma: inter-blade phase angle per harmonic (periodic meshes)."""
+    sigma: inter-blade phase angle per harmonic (periodic meshes); part:
+    partition id per node (couplings across partitions dropped)."""
     B = _f64(B)
     X = np.zeros_like(B) if X0 is None else _f64(X0).copy()
     keep = []
-    rc = _load().oracle_jacobi(*_sys_args(jac, vol, omega, sigma, keep), B.ravel(), X.reshape(-1), int(sweeps))
+    part_p = None
+    if part is not None:
+        pa = np.ascontiguousarray(part, dtype=np.int32).reshape(jac.n_nodes)
+        keep.append(pa)
+        part_p = pa.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_jacobi(*_sys_args(jac, vol, omega, sigma, keep), B.ravel(), X.reshape(-1), int(sweeps),
+                               part_p)
     if rc != 0:
         raise FloatingPointError("singular diagonal block")
     return X

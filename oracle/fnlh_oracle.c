@@ -51,6 +51,11 @@
  *    (previous).  So the off-diagonal term of harmonic l across such an edge
  *    is J_ij e^{i s sigma_l} x_j: J itself is unchanged and shared, the mean
  *    flow (plain periodicity) carries no phase.
+ *  - Domain-truncated block Jacobi (Implementation, parallel decomposition:
+ *    the entries that couple two nodes of different partitions are ignored,
+ *    so that each partition's sub-system is solved on its own): with a
+ *    partition id per node, the sweep drops J_ij x_j whenever i and j lie in
+ *    different partitions.  The residual always keeps every coupling.
  *
  * Layout: X, B, r are real [n][C][b], C = 1 + 2N; column 0 is the mean flow,
  * columns 2l-1 / 2l are Re / Im of harmonic l (omega[l-1]).  Off-diagonal
@@ -354,14 +359,16 @@ static int lu_solve_cplx(int b, cplx *M, cplx *s)
 
 /* S -= sum_j J_ij x_j over row i for every column of the [C][b] row S.  With
  * side != NULL, harmonic l takes x_j times e^{i side[p] sigma[l-1]} on the
- * entries of periodic edges (phase-lagged boundary); the mean flow never. */
+ * entries of periodic edges (phase-lagged boundary); the mean flow never.
+ * With part != NULL, neighbours in another partition than i are skipped. */
 static void subtract_offd(int i, int b, int n_harm, const int32_t *row_ptr, const int32_t *col_idx,
-                          const double *offd, const int8_t *side, const double *sigma, const double *X,
-                          double *S)
+                          const double *offd, const int8_t *side, const double *sigma, const int32_t *part,
+                          const double *X, double *S)
 {
     const int C = 1 + 2 * n_harm, bb = b * b;
     const size_t row = (size_t)C * b;
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
+        if (part && part[col_idx[p]] != part[i]) continue;
         const double *Jij = offd + (size_t)p * bb;
         const double *Xj = X + (size_t)col_idx[p] * row;
         const int s = side ? side[p] : 0;
@@ -389,12 +396,13 @@ static void subtract_offd(int i, int b, int n_harm, const int32_t *row_ptr, cons
 
 /* One undamped block-Jacobi sweep per iteration, `sweeps` iterations;
  * X holds x^0 on entry and x^sweeps on return.  side / sigma (nullable):
- * phase-lagged periodic edges (subtract_offd).  Returns -1 on a singular
- * diagonal block. */
+ * phase-lagged periodic edges; part (nullable): partition of each node,
+ * couplings across partitions dropped (subtract_offd).  Returns -1 on a
+ * singular diagonal block. */
 int oracle_jacobi(int n, int b, int n_harm, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *offd, const double *diag, const double *D, const double *vol,
                   const double *omega, const int8_t *side, const double *sigma, const double *B, double *X,
-                  int sweeps)
+                  int sweeps, const int32_t *part)
 {
     const int C = 1 + 2 * n_harm, bb = b * b;
     const size_t row = (size_t)C * b;
@@ -406,7 +414,7 @@ int oracle_jacobi(int n, int b, int n_harm, const int32_t *row_ptr, const int32_
             double S[(1 + 2 * 64) * MAXB];
             const double *Bi = B + (size_t)i * row;
             for (size_t t = 0; t < row; t++) S[t] = Bi[t];
-            subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, X, S);
+            subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, part, X, S);
             const double *Pi = diag + (size_t)i * bb;
             double *Yi = Xn + (size_t)i * row;
             /* mean flow: real system (omega = 0) */
@@ -454,7 +462,7 @@ int oracle_residual(int n, int b, int n_harm, const int32_t *row_ptr, const int3
         const double *Bi = B + (size_t)i * row;
         const double *Xi = X + (size_t)i * row;
         for (size_t t = 0; t < row; t++) R[t] = Bi[t];
-        subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, X, R);
+        subtract_offd(i, b, n_harm, row_ptr, col_idx, offd, side, sigma, NULL, X, R);
         const double *Pi = diag + (size_t)i * bb;
         for (int c = 0; c < C; c++)
             for (int rr = 0; rr < b; rr++) {

@@ -127,6 +127,18 @@ def hex_mesh(nx: int, ny: int, nz: int, seed: int = 1, perturb: float = 0.1, per
     )
 
 
+def box_partition(dims, parts) -> np.ndarray:
+    """Partition id of every node of an nx*ny*nz lattice cut into px*py*pz
+    boxes of (nearly) equal size -- the domain decomposition of a parallel
+    run, one box per processor.  Node (i, j, k) goes to box
+    (i px // nx, j py // ny, k pz // nz), numbered x fastest."""
+    nx, ny, nz = dims
+    px, py, pz = parts
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    bi, bj, bk = (i * px) // nx, (j * py) // ny, (k * pz) // nz
+    return np.ascontiguousarray((bi + px * (bj + py * bk)).ravel(), dtype=np.int32)
+
+
 def custom_mesh(positions, edge_nodes, vol=None) -> Mesh:
     """Mesh from explicit positions and edges (tiny hand-made cases)."""
     pos = np.asarray(positions, dtype=np.float64).reshape(-1, 3)

@@ -79,3 +79,15 @@ def test_permutation_preserves_graph():
     new = {tuple(sorted((perm[a], perm[b]))) for a, b in pm.edge_nodes.tolist()}
     assert old == new
     assert np.array_equal(pm.vol, m.vol[perm])
+
+
+def test_box_partition_cuts_the_lattice_into_boxes():
+    dims, parts = (10, 7, 5), (3, 2, 2)
+    part = inputs.box_partition(dims, parts)
+    assert part.dtype == np.int32 and part.shape == (10 * 7 * 5,)
+    ids, counts = np.unique(part, return_counts=True)
+    assert list(ids) == list(range(12))
+    assert counts.max() - counts.min() <= 10 * 7 * 5 // 12  # nearly equal boxes
+    # every box is a contiguous index range along each axis
+    p3 = part.reshape(5, 7, 10)
+    assert np.all(np.diff(p3 % 3, axis=2) >= 0)

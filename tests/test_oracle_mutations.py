@@ -46,6 +46,9 @@ MUTATIONS = {
     "phase_side_ignores_direction": ("side[p] = (int8_t)(nb[p].sgn * periodic[nb[p].e]);",
                                      "side[p] = (int8_t)(periodic[nb[p].e]);"),
     "phase_im_part_unrotated": (": sn * re + cs * im;", ": im;"),
+    "partition_cut_ignored": ("if (part && part[col_idx[p]] != part[i]) continue;", ""),
+    "partition_cut_inverted": ("if (part && part[col_idx[p]] != part[i]) continue;",
+                               "if (part && part[col_idx[p]] == part[i]) continue;"),
     "sylvester_wrong_index": ("double am = A[t * b + c] - ((t == c) ? lam[m] : 0.0);",
                               "double am = A[c * b + t] - ((t == c) ? lam[m] : 0.0);"),
 }

@@ -24,6 +24,10 @@ paper or by mathematics:
   behaves exactly like a ring of P identical passages joined by plain
   periodic edges whose right-hand side advances by e^{i sigma} per passage --
   sweep by sweep for Jacobi, and entry by entry for the residual.
+* Domain truncation (couplings across partitions dropped in the sweep): one
+  partition is plain Jacobi, bit for bit; converged truncated Jacobi equals
+  independent dense solves of every partition's diagonal sub-matrix; with
+  one node per partition one sweep is already the fixed point.
 """
 
 import numpy as np
@@ -555,3 +559,44 @@ def test_phase_lagged_residual_equals_ring():
     ref = phase_shift(r, N, sigma, P)
     assert np.allclose(rr, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     assert np.allclose(rnorms, P * norms, rtol=1e-12)
+
+
+# ------------------------------------------------------ domain truncation
+
+def test_one_partition_is_plain_jacobi():
+    mesh, jac, B, om = small_problem(dims=(5, 4, 3), block=6, n_harm=2)
+    x0 = np.random.default_rng(21).normal(size=B.shape)
+    a = oracle.jacobi(jac, mesh.vol, om, B, 7, X0=x0)
+    b = oracle.jacobi(jac, mesh.vol, om, B, 7, X0=x0, part=np.zeros(mesh.n_nodes, np.int32))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("parts", [(2, 1, 1), (2, 2, 1), (3, 2, 2)])
+def test_truncated_jacobi_solves_each_partition(parts):
+    dims = (6, 4, 4)
+    mesh, jac, B, om = small_problem(dims=dims, block=5, n_harm=2)
+    part = inputs.box_partition(dims, parts)
+    assert len(np.unique(part)) == parts[0] * parts[1] * parts[2]
+    X = oracle.jacobi(jac, mesh.vol, om, B, 600, part=part)
+    got = _dense.split_systems(X, len(om))
+    bs = _dense.split_systems(B, len(om))
+    b = jac.block
+    for k, w in enumerate(_systems(jac, mesh.vol, om)):
+        A = _dense.dense_operator(jac.row_ptr, jac.col_idx, jac.offd, jac.diag, jac.D, mesh.vol, w)
+        for q in np.unique(part):
+            idx = np.concatenate([np.arange(i * b, (i + 1) * b) for i in np.flatnonzero(part == q)])
+            xq = np.linalg.solve(A[np.ix_(idx, idx)], bs[k][idx])
+            assert np.linalg.norm(got[k][idx] - xq) <= 1e-12 * np.linalg.norm(xq), (k, q)
+
+
+def test_single_node_partitions_fix_after_one_sweep():
+    mesh, jac, B, om = small_problem(dims=(4, 3, 3), block=6, n_harm=1)
+    part = np.arange(mesh.n_nodes, dtype=np.int32)
+    X1 = oracle.jacobi(jac, mesh.vol, om, B, 1, part=part)
+    X2 = oracle.jacobi(jac, mesh.vol, om, B, 2, part=part)
+    assert np.array_equal(X1, X2)
+    b = jac.block
+    for i in range(mesh.n_nodes):
+        M = jac.diag[i] + (jac.D[i] + 1j * om[0] * mesh.vol[i]) * np.eye(b)
+        y = np.linalg.solve(M, B[i, 1] + 1j * B[i, 2])
+        assert np.allclose(X1[i, 1] + 1j * X1[i, 2], y, rtol=1e-13, atol=1e-14 * np.abs(y).max())
