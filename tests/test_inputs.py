@@ -87,7 +87,11 @@ def test_box_partition_cuts_the_lattice_into_boxes():
     assert part.dtype == np.int32 and part.shape == (10 * 7 * 5,)
     ids, counts = np.unique(part, return_counts=True)
     assert list(ids) == list(range(12))
-    assert counts.max() - counts.min() <= 10 * 7 * 5 // 12  # nearly equal boxes
-    # every box is a contiguous index range along each axis
+    # each axis is cut into contiguous index ranges whose lengths differ by at most one
     p3 = part.reshape(5, 7, 10)
-    assert np.all(np.diff(p3 % 3, axis=2) >= 0)
+    for axis, (n, q, stride) in enumerate(((10, 3, 1), (7, 2, 3), (5, 2, 6))):
+        line = np.moveaxis(p3, 2 - axis, 0)[:, 0, 0] if axis else p3[0, 0, :]
+        box = (line // stride) % q
+        assert np.all(np.diff(box) >= 0) and set(box) == set(range(q))
+        lengths = np.bincount(box)
+        assert lengths.max() - lengths.min() <= 1, (axis, lengths)
