@@ -344,6 +344,8 @@ def run_fnlh(args):
         line["rk_stages"] = rk_section(torch, fnlh, inputs, dev)
         torch.cuda.empty_cache()
         line["periodic"] = periodic_section(torch, fnlh, inputs, dev)
+        torch.cuda.empty_cache()
+        line["partitions"] = partition_section(torch, fnlh, inputs, dev)
         if not args.no_large:
             torch.cuda.empty_cache()
             line["large"] = large_section(torch, fnlh, inputs, dev)
@@ -450,7 +452,7 @@ def periodic_section(torch, fnlh, inputs, dev):
         p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=WORKLOAD,
                            periodic=periodic)
         dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-        J = fnlh.DeviceJacobian(dm, p.block, prep | (fnlh.FNLH_PREP_PERIODIC if periodic else 0), dev)
+        J = fnlh.DeviceJacobian(dm, p.block, prep | (fnlh.FNLH_PREP_TAGS if periodic else 0), dev)
         fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
         B = torch.from_numpy(p.b).to(dev)
         X = torch.zeros_like(B)
@@ -471,6 +473,41 @@ def periodic_section(torch, fnlh, inputs, dev):
         torch.cuda.empty_cache()
     for name in ("f64", "f32", "bf16"):
         out[f"{name}_overhead"] = out["periodic"][f"{name}_sweep_ms"] / out["plain"][f"{name}_sweep_ms"] - 1.0
+    return out
+
+
+def partition_section(torch, fnlh, inputs, dev, tol=1e-8, inner=12):
+    """Domain-truncated sweeps (the paper's parallel decomposition drops the
+    couplings between partitions) on the measured passage cut into 1 to 4,096
+    boxes: FP32 defect correction to a 1e-8 FP64 residual -- the full residual
+    wins back what the truncated sweeps leave out -- and its cost as the
+    boxes shrink."""
+    c = inputs.CONFIGS[WORKLOAD]
+    p = inputs.config_problem(WORKLOAD)
+    n = p.mesh.n_nodes
+    B = torch.from_numpy(p.b).to(dev)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(n, p.block, p.n_harm, dev)
+    out = {"workload": f"{WORKLOAD}: FP32 blocks, {inner} truncated inner sweeps per FP64 residual, "
+                       f"to {tol:g}; boxes px x py x pz of the 128x64x48 lattice"}
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    for parts in ((1, 1, 1), (2, 2, 2), (4, 4, 4), (8, 8, 8), (16, 16, 16)):
+        part = inputs.box_partition(c["dims"], parts)
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev, part=part)
+        J = fnlh.DeviceJacobian(dm, p.block, fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_TAGS, dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, tol, inner, 200, ws=ws,
+                                                  raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        nparts = parts[0] * parts[1] * parts[2]
+        out[f"parts_{nparts}"] = {"nodes_per_part": n // nparts, "status": fnlh.fnlh_strerror(st), "checks": checks,
+                                  "sweeps": sweeps, "seconds": t, "max_rel_residual": float(np.max(rel))}
+        del dm, J
+        torch.cuda.empty_cache()
     return out
 
 

@@ -83,9 +83,10 @@ enum fnlh_prep_flags {
     FNLH_PREP_F64 = 1,
     FNLH_PREP_F32 = 2,
     FNLH_PREP_BF16 = 4,
-    /* a copy of col_idx whose top two bits carry each entry's passage
-     * offset: required by every call on a mesh with `periodic` edges */
-    FNLH_PREP_PERIODIC = 8
+    /* a copy of col_idx whose top three bits tag each entry: the passage
+     * offset of a periodic edge, and whether it crosses a partition; required
+     * by every call on a mesh with `periodic` or `part` */
+    FNLH_PREP_TAGS = 8
 };
 
 #define FNLH_MAX_HARMONICS 64
@@ -105,8 +106,16 @@ typedef struct fnlh_mesh {
      * periodic boundary: +1 the next passage, -1 the previous, 0 none (an
      * ordinary edge); other values count by their sign.  The normal of such
      * an edge points to the image of j.  Needs a prep blob with
-     * FNLH_PREP_PERIODIC.  (Every mesh needs n_nodes < 2^30.) */
+     * FNLH_PREP_TAGS.  (Every mesh needs n_nodes < 2^29.) */
     const int8_t *periodic;
+    /* [n] nullable: partition of each node -- the domain decomposition of a
+     * parallel run.  As in the paper's decomposition (Implementation: the
+     * entries that couple nodes of different partitions are ignored), the
+     * sweeps drop every coupling between partitions, so each partition
+     * relaxes on its own, while the residual keeps them all; fnlh_solve then
+     * corrects the truncated sweeps with the full residual at every
+     * precision.  Needs FNLH_PREP_TAGS. */
+    const int32_t *part;
 } fnlh_mesh;
 
 /* Jacobian construction parameters. */
@@ -191,9 +200,9 @@ int fnlh_build_jacobian(const fnlh_mesh *mesh, const double *Q, const fnlh_param
 /* Derived data for the sweeps: per node an orthogonal Q_i with
  * Q_i^T (J_ii + D_i I) Q_i upper Hessenberg, and the off-diagonal blocks
  * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags;
- * with FNLH_PREP_PERIODIC the passage-tagged column copy (from the mesh's
- * periodic flags; FNLH_ERR_WORKSPACE when the mesh has periodic edges and
- * the flag is missing).  Depends only on J, D and the mesh, so it is
+ * with FNLH_PREP_TAGS the tagged column copy (from the mesh's periodic flags
+ * and partition; FNLH_ERR_WORKSPACE when the mesh has either and the flag is
+ * missing).  Depends only on J, D and the mesh, so it is
  * independent of the number of harmonics and of their phase angles.
  * Call after changing offd/diag/D yourself.  Asynchronous. */
 int fnlh_prepare(const fnlh_mesh *mesh, fnlh_jacobian *J, fnlh_stream_t stream);
@@ -232,7 +241,9 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
  * FNLH_F32 / FNLH_BF16: defect correction -- FP64 residual r = B - A x,
  * `inner_sweeps` sweeps on A e = r with the low-precision blocks and FP32
  * arithmetic from e = 0 (r and e rotated in FP32), then x += e with the sum in
- * FP64; repeated.  X: in x0 (ignored with FNLH_SOLVE_ZERO_GUESS), out x.
+ * FP64; repeated.  On a mesh with `part` the FP64 solve is a defect
+ * correction too (inner FP64 sweeps without the cross-partition couplings,
+ * FP64 residual with them).  X: in x0 (ignored with FNLH_SOLVE_ZERO_GUESS), out x.
  * SYNCHRONISING (reads the norms after every check).  Outputs (host, each
  * nullable): *checks_done residual evaluations, *sweeps_done total sweeps,
  * rel_res [K] final ||r_k||/||B_k||.  Returns FNLH_ERR_NOT_CONVERGED after

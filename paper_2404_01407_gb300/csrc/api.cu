@@ -38,17 +38,17 @@ int check_mesh(const fnlh_mesh* m, bool need_edges) {
   if (m->n_nodes > 0 && (!m->row_ptr || !m->vol)) return FNLH_ERR_ARG;
   if (m->n_edges > 0 && !m->col_idx) return FNLH_ERR_ARG;
   if (need_edges && m->n_edges > 0 && (!m->csr_edge || !m->edge_nodes || !m->normals)) return FNLH_ERR_ARG;
-  // node ids must leave the top two bits free: the kernels read them as the
-  // passage tags of periodic edges
+  // node ids must leave the top three bits free: the kernels read them as the
+  // tags of periodic edges and partition cuts
   if (m->n_nodes > (int32_t)kColMask) return FNLH_ERR_UNSUPPORTED;
   return FNLH_OK;
 }
 
-// A mesh with periodic edges is only read through the prep blob's tagged
-// column copy.
-int check_periodic(const fnlh_mesh* m, const fnlh_jacobian* J) {
-  if (!m->periodic) return FNLH_OK;
-  if (!J->prep || !J->prep_ready || !(J->prep_flags & FNLH_PREP_PERIODIC)) return FNLH_ERR_WORKSPACE;
+// A mesh with periodic edges or partitions is only read through the prep
+// blob's tagged column copy.
+int check_tags(const fnlh_mesh* m, const fnlh_jacobian* J) {
+  if (!tagged_mesh(m)) return FNLH_OK;
+  if (!J->prep || !J->prep_ready || !(J->prep_flags & FNLH_PREP_TAGS)) return FNLH_ERR_WORKSPACE;
   if (!aligned(J->prep, 256)) return FNLH_ERR_ARG;
   if (J->prep_bytes < fnlh_prep_bytes(J->n_nodes, J->nnz, J->block, J->prep_flags)) return FNLH_ERR_WORKSPACE;
   return FNLH_OK;
@@ -193,12 +193,10 @@ int fnlh_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, fnlh_stream_t stream) 
   FNLH_TRY(check_jac(mesh, J));
   if (!J->prep) return FNLH_ERR_WORKSPACE;
   if (!aligned(J->prep, 256)) return FNLH_ERR_ARG;
-  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16 | FNLH_PREP_PERIODIC)) return FNLH_ERR_ARG;
+  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16 | FNLH_PREP_TAGS)) return FNLH_ERR_ARG;
   if (J->prep_bytes < fnlh_prep_bytes(J->n_nodes, J->nnz, J->block, J->prep_flags)) return FNLH_ERR_WORKSPACE;
-  if (mesh->periodic) {
-    if (!(J->prep_flags & FNLH_PREP_PERIODIC)) return FNLH_ERR_WORKSPACE;
-    FNLH_TRY(check_mesh(mesh, true));  // the tags come from csr_edge and edge_nodes
-  }
+  if (tagged_mesh(mesh) && !(J->prep_flags & FNLH_PREP_TAGS)) return FNLH_ERR_WORKSPACE;
+  if (mesh->periodic) FNLH_TRY(check_mesh(mesh, true));  // passage tags come from csr_edge and edge_nodes
   FNLH_TRY(prepare_impl(mesh, J, (cudaStream_t)stream));
   J->prep_ready = 1;
   return FNLH_OK;
@@ -212,7 +210,7 @@ int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   if (!valid_precision(precision) || sweeps < 0) return FNLH_ERR_ARG;
   FNLH_TRY(check_systems(n_harm, omega, sigma));
   FNLH_TRY(check_prep(J, precision));
-  FNLH_TRY(check_periodic(mesh, J));
+  FNLH_TRY(check_tags(mesh, J));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
@@ -225,7 +223,7 @@ int fnlh_residual(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm,
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, sigma));
-  FNLH_TRY(check_periodic(mesh, J));
+  FNLH_TRY(check_tags(mesh, J));
   if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
   if (!workspace) return FNLH_ERR_WORKSPACE;
   if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
@@ -245,7 +243,7 @@ int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
   FNLH_TRY(check_systems(n_harm, omega, sigma));
   FNLH_TRY(check_prep(J, precision));
-  FNLH_TRY(check_periodic(mesh, J));
+  FNLH_TRY(check_tags(mesh, J));
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
@@ -265,7 +263,7 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
     FNLH_TRY(check_jac(R.mesh, R.J));
     FNLH_TRY(check_systems(R.n_harm, R.omega, R.sigma));
     FNLH_TRY(check_prep(R.J, precision));
-    FNLH_TRY(check_periodic(R.mesh, R.J));
+    FNLH_TRY(check_tags(R.mesh, R.J));
     if (R.mesh->n_nodes > 0 && (!R.B || !R.X)) return FNLH_ERR_ARG;
     FNLH_TRY(check_pairs(R.mesh->n_nodes, R.n_harm));
     need += ws_layout(R.mesh->n_nodes, R.J->block, R.n_harm, precision).total;
@@ -282,7 +280,7 @@ int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, sigma));
-  FNLH_TRY(check_periodic(mesh, J));
+  FNLH_TRY(check_tags(mesh, J));
   if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
   const Systems sys = make_systems(n_harm, omega, sigma);
   return residual_noalloc_launch(mesh, J, sys, B, X, r, norms, (cudaStream_t)stream);

@@ -21,13 +21,17 @@ struct Systems {
   double2 phase[kMaxSys];  // (cos, sin) of the inter-blade phase angle; phase[0] = (1, 0)
 };
 
-// Column entries of a periodic mesh (the prep blob's tagged copy of col_idx)
-// carry the neighbour's blade passage in their top two bits: 1 = the next
-// passage (factor e^{+i sigma_k} on x_j), 2 = the previous one (e^{-i sigma_k}).
-constexpr uint32_t kColMask = 0x3fffffffu;
+// Column entries of a tagged mesh (the prep blob's copy of col_idx) carry the
+// neighbour's blade passage in their top two bits -- 1 = the next passage
+// (factor e^{+i sigma_k} on x_j), 2 = the previous one (e^{-i sigma_k}) -- and
+// in bit 29 whether the neighbour lies in another partition (a coupling the
+// sweeps drop and the residual keeps).
+constexpr uint32_t kColMask = 0x1fffffffu;
 constexpr uint32_t kSideNext = 1u, kSidePrev = 2u;
+constexpr uint32_t kCutBit = 1u << 29;
 __host__ __device__ __forceinline__ int col_of(int c) { return (int)((uint32_t)c & kColMask); }
 __host__ __device__ __forceinline__ uint32_t side_of(int c) { return (uint32_t)c >> 30; }
+__host__ __device__ __forceinline__ bool cut_of(int c) { return ((uint32_t)c & kCutBit) != 0; }
 
 // x <- e^{+-i sigma} x for a neighbour across the periodic boundary (side
 // kSideNext: +, kSidePrev: -), ph = (cos sigma, sin sigma).
@@ -244,7 +248,7 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
 // hessf [n][b][b] f32   (when an F32/BF16 copy is requested)
 // rotf  [n][b][b] f32   Q_i in FP32 (same condition: the mixed solve's rotations)
 // offd64 / offd32 / offd16 [nnz][b][b] rotated off-diagonal copies
-// cols  [nnz] int32     col_idx with the passage tags (FNLH_PREP_PERIODIC)
+// cols  [nnz] int32     col_idx with the passage and partition tags (FNLH_PREP_TAGS)
 struct PrepLayout {
   size_t rot, hess, hessf, rotf, offd64, offd32, offd16, cols, total;
 };
@@ -276,7 +280,7 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
     p.offd16 = off;
     off = align256(off + (size_t)nnz * bb * 2);
   }
-  if (flags & FNLH_PREP_PERIODIC) {
+  if (flags & FNLH_PREP_TAGS) {
     p.cols = off;
     off = align256(off + (size_t)nnz * 4);
   }
@@ -287,10 +291,11 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
 template <typename T> inline T* at(void* base, size_t off) { return reinterpret_cast<T*>((char*)base + off); }
 
 // The column array the sweeps and the residual read: the mesh's own, or on a
-// mesh with periodic edges the passage-tagged copy in the prep blob (the
+// mesh with periodic edges or partitions the tagged copy in the prep blob (the
 // entry points check that it exists before anything launches).
+inline bool tagged_mesh(const fnlh_mesh* m) { return m->periodic != nullptr || m->part != nullptr; }
 inline const int32_t* csr_columns(const fnlh_mesh* m, const fnlh_jacobian* J) {
-  if (!m->periodic) return m->col_idx;
+  if (!tagged_mesh(m)) return m->col_idx;
   const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
   return at<int32_t>(J->prep, L.cols);
 }

@@ -275,16 +275,17 @@ __global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, con
     }
 }
 
-// Passage-tagged copy of col_idx (phase-lagged periodic edges), one thread
-// per row: entry p of row i across edge e gets the passage offset of its
-// neighbour as seen from i -- periodic[e] when i is the edge's first node,
-// its opposite otherwise -- in the top two bits.  No periodic array: an
-// untagged copy.
+// Tagged copy of col_idx, one thread per row: entry p of row i across edge e
+// gets the passage offset of its neighbour as seen from i (phase-lagged
+// periodic edges) -- periodic[e] when i is the edge's first node, its
+// opposite otherwise -- in the top two bits, and the cut bit when the
+// neighbour lies in another partition.  Neither array: an untagged copy.
 __global__ void __launch_bounds__(128) k_tag_columns(int32_t n, const int32_t* __restrict__ row_ptr,
                                                      const int32_t* __restrict__ col_idx,
                                                      const int32_t* __restrict__ csr_edge,
                                                      const int32_t* __restrict__ edge_nodes,
-                                                     const int8_t* __restrict__ periodic, int32_t* __restrict__ cols) {
+                                                     const int8_t* __restrict__ periodic,
+                                                     const int32_t* __restrict__ part, int32_t* __restrict__ cols) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(128) k_tag_columns(int32_t n, const int32_t* _
       if (edge_nodes[2 * e] != i) side = -side;
       tag = side > 0 ? (kSideNext << 30) : (side < 0 ? (kSidePrev << 30) : 0u);
     }
+    if (part && part[col_idx[p]] != part[i]) tag |= kCutBit;
     cols[p] = (int32_t)((uint32_t)col_idx[p] | tag);
   }
 }
@@ -329,7 +331,7 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   }
   if (L.cols != (size_t)-1 && n > 0) {
     k_tag_columns<<<(n + 127) / 128, 128, 0, s>>>(n, mesh->row_ptr, mesh->col_idx, mesh->csr_edge, mesh->edge_nodes,
-                                                  mesh->periodic, at<int32_t>(J->prep, L.cols));
+                                                  mesh->periodic, mesh->part, at<int32_t>(J->prep, L.cols));
     FNLH_LAUNCH_CHECK();
   }
   return FNLH_OK;

@@ -399,10 +399,14 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   bool conv = false;
   const bool mixed = precision != FNLH_F64;
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
+  // On a partitioned mesh the sweeps drop the cross-partition couplings, so
+  // plain FP64 Jacobi would converge to the truncated system: there the FP64
+  // solve is a defect correction too, against the full FP64 residual.
+  const bool defect = mixed || m->part != nullptr;
   uint64_t active[2] = {~0ull, ~0ull};
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
   if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
-  if (!mixed) {
+  if (!defect) {
     // plain FP64 Jacobi: iterate in the rotated basis, check every `inner` sweeps
     if ((rc = rotate_in<BS, T>(n, K, op.rot, B, v0, s))) return rc;
     if ((rc = rotate_in<BS, T>(n, K, op.rot, X, v1, s))) return rc;
@@ -410,8 +414,9 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   T* cur = v1;
   FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   for (;;) {
-    rc = residual_launch(m, J, sys, B, X, nullptr, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms,
-                         ws, s);
+    // mixed: Q^T r in FP32 straight into v0; FP64 defect correction: r into v2
+    double* r64 = (defect && !mixed) ? (double*)v2 : nullptr;
+    rc = residual_launch(m, J, sys, B, X, r64, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms, ws, s);
     x_zero = false;
     if (rc) return rc;
     int32_t hstatus = 0;
@@ -430,13 +435,20 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
         if (ck.rel[k] <= tol) active[k >> 6] &= ~(1ull << (k & 63));
     const uint64_t* act = masking ? active : nullptr;
     T* res = nullptr;
-    if (mixed) {
+    if (defect) {
       // inner: A~ e = r~ from e = 0 (v1/v2 ping-pong), then x += Q e in FP64
+      if constexpr (sizeof(T) == 8) {
+        if ((rc = rotate_in<BS, T>(n, K, op.rot, (const double*)v2, v0, s))) return rc;
+      }
       if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res, act))) return rc;
       const long long count = (long long)n * K;
-      if (count > 0) {
-        k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X);
-        FNLH_LAUNCH_CHECK();
+      if constexpr (sizeof(T) == 4) {
+        if (count > 0) {
+          k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X);
+          FNLH_LAUNCH_CHECK();
+        }
+      } else {
+        if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 1, s))) return rc;
       }
     } else {
       T* other = (cur == v1) ? v2 : v1;

@@ -214,7 +214,7 @@ struct TileRow {
   FastDiv divK;      // division by K (pair index -> node), n K < 2^31
   int32_t stage;     // 1: stage the tile's blocks in shared memory when they fit
   const int32_t* row_ptr;
-  const int32_t* col_idx;  // possibly passage-tagged (col_of / side_of)
+  const int32_t* col_idx;  // possibly tagged (col_of / side_of / cut_of)
   const void* offd;  // rotated off-diagonal blocks (TJ)
   const void* hess;  // [n][b][b] (double for FP64 sweeps, float otherwise)
   const double* vol;
@@ -268,6 +268,7 @@ __device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& 
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
       const int cj = __ldg(R.col_idx + p);
+      if (cut_of(cj)) continue;  // coupling to another partition: dropped
       Cvec<BS, double> x;
       load_slice<BS>(X + ((size_t)col_of(cj) * R.K + k) * 2 * BS, x);
       if (side_of(cj)) phase_shift<BS, double>(x.re, x.im, side_of(cj), io.phase[k]);
@@ -305,7 +306,9 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
     const double* __restrict__ offd = (const double*)R.offd;
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
-      const int j = col_of(__ldg(R.col_idx + p));  // the mean flow carries no phase
+      const int cj = __ldg(R.col_idx + p);
+      if (cut_of(cj)) continue;
+      const int j = col_of(cj);  // the mean flow carries no phase
       const double* xs = X + (size_t)j * R.K * 2 * BS;
       double xr[BS];
 #pragma unroll
@@ -457,21 +460,20 @@ __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& 
       // software pipeline: the next neighbour's slice is in flight while the
       // current one is multiplied
       Cvec<BS, float> xn;
-      uint32_t side_n = 0;
+      int cn = 0;  // tagged column of the slice in flight
       if (p0 < p1) {
-        const int cj = staged ? sC[p0 - p_first] : __ldg(R.col_idx + p0);
-        side_n = side_of(cj);
-        load_slice<BS>(Xk + (size_t)col_of(cj) * stride, xn);
+        cn = staged ? sC[p0 - p_first] : __ldg(R.col_idx + p0);
+        load_slice<BS>(Xk + (size_t)col_of(cn) * stride, xn);
       }
       for (int p = p0; p < p1; ++p) {
         Cvec<BS, float> x = xn;
-        const uint32_t side = side_n;
+        const int cj = cn;
         if (p + 1 < p1) {
-          const int cj = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
-          side_n = side_of(cj);
-          load_slice<BS>(Xk + (size_t)col_of(cj) * stride, xn);
+          cn = staged ? sC[p + 1 - p_first] : __ldg(R.col_idx + p + 1);
+          load_slice<BS>(Xk + (size_t)col_of(cn) * stride, xn);
         }
-        if (side) phase_shift<BS, float>(x.re, x.im, side, io.phase[k]);
+        if (cut_of(cj)) continue;  // coupling to another partition: dropped
+        if (side_of(cj)) phase_shift<BS, float>(x.re, x.im, side_of(cj), io.phase[k]);
         if (staged) spmv_rows_smem<BS>(sJ + (size_t)(p - p_first) * BS * BS, x, s);
         else spmv_rows_global<BS, TJ>((const TJ*)R.offd + (size_t)p * BS * BS, x, s);
       }

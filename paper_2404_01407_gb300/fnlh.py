@@ -36,7 +36,7 @@ FNLH_ERR_NOT_CONVERGED = -8
 FNLH_ERR_BAD_MESH = -9
 
 FNLH_F64, FNLH_F32, FNLH_BF16 = 0, 1, 2
-FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16, FNLH_PREP_PERIODIC = 1, 2, 4, 8
+FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16, FNLH_PREP_TAGS = 1, 2, 4, 8
 PRECISIONS = {"f64": FNLH_F64, "f32": FNLH_F32, "bf16": FNLH_BF16}
 PREP_FOR = {FNLH_F64: FNLH_PREP_F64, FNLH_F32: FNLH_PREP_F32, FNLH_BF16: FNLH_PREP_BF16}
 MAX_HARMONICS = 64
@@ -44,7 +44,8 @@ MAX_HARMONICS = 64
 
 class fnlh_mesh(ctypes.Structure):
     _fields_ = [("n_nodes", c_i32), ("n_edges", c_i32), ("edge_nodes", c_vp), ("normals", c_vp),
-                ("vol", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("csr_edge", c_vp), ("periodic", c_vp)]
+                ("vol", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("csr_edge", c_vp), ("periodic", c_vp),
+                ("part", c_vp)]
 
 
 class fnlh_params(ctypes.Structure):
@@ -180,7 +181,7 @@ def _sigma(sigma, n_harm):
 class DeviceMesh:
     """Mesh arrays on the device plus the ctypes fnlh_mesh describing them."""
 
-    def __init__(self, n_nodes, edge_nodes, normals, vol, device="cuda", periodic=None):
+    def __init__(self, n_nodes, edge_nodes, normals, vol, device="cuda", periodic=None, part=None):
         en = np.ascontiguousarray(edge_nodes, dtype=np.int32).reshape(-1, 2)
         n_edges = en.shape[0]
         row_ptr = np.zeros(n_nodes + 1, dtype=np.int32)
@@ -200,13 +201,18 @@ class DeviceMesh:
         if periodic is not None:
             per = np.ascontiguousarray(periodic, dtype=np.int8).reshape(n_edges)
             self.periodic = torch.from_numpy(per).to(dev) if n_edges else None
+        self.part = None
+        if part is not None:
+            self.part = torch.from_numpy(np.ascontiguousarray(part, dtype=np.int32).reshape(n_nodes)).to(dev)
         self.c = fnlh_mesh(self.n_nodes, self.n_edges, _ptr(self.edge_nodes), _ptr(self.normals), _ptr(self.vol),
-                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.csr_edge), _ptr(self.periodic))
+                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.csr_edge), _ptr(self.periodic),
+                           _ptr(self.part))
 
     @classmethod
-    def from_mesh(cls, mesh, device="cuda"):
+    def from_mesh(cls, mesh, device="cuda", part=None):
+        """part: partition id per node (domain-truncated sweeps), or None."""
         return cls(mesh.n_nodes, mesh.edge_nodes, mesh.normals, mesh.vol, device,
-                   periodic=getattr(mesh, "periodic", None))
+                   periodic=getattr(mesh, "periodic", None), part=part)
 
 
 class DeviceJacobian:

@@ -103,9 +103,9 @@ def test_validation_rejects_before_launch():
         == fnlh.FNLH_ERR_ARG
 
 
-def test_periodic_validation_rejects_before_launch():
-    """Phase-lagged periodic edges: the tagged column copy must be in the prep
-    blob, node ids must leave the top two bits free, phase angles finite."""
+def test_tagged_mesh_validation_rejects_before_launch():
+    """Periodic edges and partitions: the tagged column copy must be in the
+    prep blob, node ids must leave the top three bits free, phase angles finite."""
     L = fnlh.lib()
     per = ctypes.c_void_p(4096)  # never dereferenced: validation fails first
     vol = ctypes.c_void_p(256)
@@ -122,15 +122,20 @@ def test_periodic_validation_rejects_before_launch():
     assert L.fnlh_relax(ctypes.byref(m), ctypes.byref(Jp), 1, om, None, vol, vol, 1, 0, vol, 1 << 20, None) \
         == fnlh.FNLH_ERR_WORKSPACE
     assert L.fnlh_prepare(ctypes.byref(m), ctypes.byref(Jp), None) == fnlh.FNLH_ERR_WORKSPACE
+    # a partitioned mesh also reads the tagged copy
+    mp = fnlh.fnlh_mesh(4, 0, None, None, vol, vol, None, None, None, ctypes.c_void_p(4096))
+    assert L.fnlh_relax(ctypes.byref(mp), ctypes.byref(Jp), 1, om, None, vol, vol, 1, 0, vol, 1 << 20, None) \
+        == fnlh.FNLH_ERR_WORKSPACE
+    assert L.fnlh_prepare(ctypes.byref(mp), ctypes.byref(Jp), None) == fnlh.FNLH_ERR_WORKSPACE
     # a non-finite phase angle
     assert L.fnlh_relax(ctypes.byref(m), ctypes.byref(J5), 2, om, sig, vol, vol, 1, 0, vol, 1 << 20, None) \
         == fnlh.FNLH_ERR_ARG
-    # node ids above 2^30 - 1 cannot leave room for the passage tags (any mesh)
-    big = fnlh.fnlh_mesh(1 << 30, 0, None, None, vol, vol, None, None, None)
-    Jb = fnlh.fnlh_jacobian(1 << 30, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
+    # node ids of 2^29 and up leave no room for the column tags (any mesh)
+    big = fnlh.fnlh_mesh(1 << 29, 0, None, None, vol, vol, None, None, None)
+    Jb = fnlh.fnlh_jacobian(1 << 29, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
     assert L.fnlh_residual(ctypes.byref(big), ctypes.byref(Jb), 0, om, None, vol, vol, None, vol, vol, 1 << 20,
                            None) == fnlh.FNLH_ERR_UNSUPPORTED
     # the tagged copy adds nnz int32 (256-aligned) to the blob
     n, nnz = 1000, 6000
-    assert fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_PERIODIC) == \
+    assert fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_TAGS) == \
         fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64) + ((nnz * 4 + 255) // 256) * 256

@@ -21,7 +21,7 @@ from tests import _gpu
 
 pytestmark = pytest.mark.gpu
 
-PREP = _gpu.ALL_PREP | fnlh.FNLH_PREP_PERIODIC
+PREP = _gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS
 
 CASES = {
     # ragged sizes: several 256-thread tiles plus a tail
@@ -197,7 +197,7 @@ def test_periodic_full_size_equals_ring():
     c = inputs.CONFIGS["c2"]
     sigma = 2.0 * np.pi * np.array([1, 2, 1, 2], dtype=np.float64) / P
     p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], name="c2_periodic", periodic=True, phase=sigma)
-    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_PERIODIC)
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_TAGS)
     X = torch.zeros_like(B)
     fnlh.fnlh_relax(dm, J, p.omega, B, X, 50, fnlh.FNLH_F64, sigma=sigma)
     x = X.cpu().numpy()
