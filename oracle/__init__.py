@@ -88,6 +88,13 @@ def _bind(lib):
     lib.oracle_jacobi.restype = ctypes.c_int
     lib.oracle_residual.argtypes = common + [_f64p, ctypes.c_void_p, _f64p]
     lib.oracle_residual.restype = ctypes.c_int
+    lib.oracle_ilu_factor.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p,
+                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, _i32p,
+                                      _f64p, _f64p]
+    lib.oracle_ilu_factor.restype = ctypes.c_int
+    lib.oracle_ilu_apply.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_void_p, _i32p, _f64p, _f64p,
+                                     _f64p, _f64p]
+    lib.oracle_ilu_apply.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
     return lib
@@ -263,3 +270,83 @@ def solve_to_tol(jac: Jacobian, vol, omega, B, tol: float, chunk: int = 10, max_
         if np.all(rel_residuals(jac, vol, omega, B, X, sigma=sigma) <= tol):
             break
     return X, done
+
+
+# ------------------------------------------------------------------ ILU(0)
+
+def elimination_rank(color) -> np.ndarray:
+    """Position of every node in the multicolour elimination order: all nodes of
+    colour 0 by increasing id, then colour 1, ..."""
+    color = np.asarray(color, dtype=np.int64)
+    order = np.lexsort((np.arange(color.shape[0]), color))
+    rank = np.empty(color.shape[0], dtype=np.int32)
+    rank[order] = np.arange(color.shape[0], dtype=np.int32)
+    return rank
+
+
+def _ptr_or_none(arr, dtype, keep):
+    if arr is None:
+        return None
+    a = np.ascontiguousarray(arr, dtype=dtype)
+    keep.append(a)
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ilu_factor(jac: Jacobian, vol, omega_k: float, rank, sigma_k: float = 0.0, part=None):
+    """Block ILU(0) of one system (omega_k, phase angle sigma_k) in the order
+    `rank`; returns (U_ii [n][b][b], L_ij or U_ij per CSR entry [nnz][b][b]),
+    complex."""
+    b, n = jac.block, jac.n_nodes
+    keep = []
+    Fd = np.zeros(max(n, 1) * b * b * 2)
+    Fo = np.zeros(max(jac.nnz, 1) * b * b * 2)
+    offd = _f64(jac.offd).ravel() if jac.nnz else np.zeros(1)
+    col = jac.col_idx if jac.nnz else np.zeros(1, dtype=np.int32)
+    rc = _load().oracle_ilu_factor(n, b, jac.row_ptr, col, offd, _f64(jac.diag).ravel(), _f64(jac.D), _f64(vol),
+                                   float(omega_k), _ptr_or_none(jac.side, np.int8, keep), float(sigma_k),
+                                   _ptr_or_none(part, np.int32, keep), np.ascontiguousarray(rank, dtype=np.int32),
+                                   Fd, Fo)
+    if rc != 0:
+        raise FloatingPointError("ILU(0): zero pivot")
+    Fd = Fd[: n * b * b * 2].view(np.complex128).reshape(n, b, b)
+    Fo = Fo[: jac.nnz * b * b * 2].view(np.complex128).reshape(jac.nnz, b, b)
+    return Fd, Fo
+
+
+def ilu_apply(jac: Jacobian, rank, factors, r, part=None) -> np.ndarray:
+    """y = (L U)^-1 r for one system's factors; r complex [n][b]."""
+    b, n = jac.block, jac.n_nodes
+    keep = []
+    Fd, Fo = factors
+    rr = np.ascontiguousarray(r, dtype=np.complex128).reshape(n * b)
+    y = np.zeros(n * b, dtype=np.complex128)
+    col = jac.col_idx if jac.nnz else np.zeros(1, dtype=np.int32)
+    fo = Fo.view(np.float64).ravel() if jac.nnz else np.zeros(2)
+    rc = _load().oracle_ilu_apply(n, b, jac.row_ptr, col, _ptr_or_none(part, np.int32, keep),
+                                  np.ascontiguousarray(rank, dtype=np.int32), np.ascontiguousarray(Fd).view(np.float64).ravel(),
+                                  np.ascontiguousarray(fo), rr.view(np.float64), y.view(np.float64))
+    if rc != 0:
+        raise FloatingPointError("ILU(0): singular pivot block")
+    return y.reshape(n, b)
+
+
+def ilu_iterate(jac: Jacobian, vol, omega, B, iterations: int, color, X0=None, sigma=None, part=None):
+    """`iterations` ILU(0) iterations x <- x + (L U)^-1 (B - A x) on every system
+    (mean flow and harmonics), in the multicolour order of `color`; the
+    residual keeps every coupling, the factors drop the cross-partition ones."""
+    B = _f64(B)
+    X = np.zeros_like(B) if X0 is None else _f64(X0).copy()
+    rank = elimination_rank(color)
+    n_harm = len(omega)
+    sig = np.zeros(n_harm) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    facs = [ilu_factor(jac, vol, 0.0, rank, 0.0, part)]
+    facs += [ilu_factor(jac, vol, omega[l], rank, sig[l], part) for l in range(n_harm)]
+    for _ in range(iterations):
+        _, r = residual(jac, vol, omega, B, X, want_r=True, sigma=sigma)
+        y0 = ilu_apply(jac, rank, facs[0], r[:, 0, :].astype(np.complex128), part)
+        X[:, 0, :] += y0.real
+        for l in range(1, n_harm + 1):
+            y = ilu_apply(jac, rank, facs[l], r[:, 2 * l - 1, :] + 1j * r[:, 2 * l, :], part)
+            X[:, 2 * l - 1, :] += y.real
+            X[:, 2 * l, :] += y.imag
+    return X

@@ -501,6 +501,187 @@ int oracle_residual(int n, int b, int n_harm, const int32_t *row_ptr, const int3
     return 0;
 }
 
+/* -------------------------------------------------------------- ILU(0) */
+
+/* Complex block inverse by Gauss-Jordan elimination with partial pivoting
+ * (M destroyed).  Returns -1 on a zero pivot. */
+static int inv_cplx(int b, cplx *M, cplx *Minv)
+{
+    for (int r = 0; r < b; r++)
+        for (int c = 0; c < b; c++) Minv[r * b + c] = (r == c) ? 1.0 : 0.0;
+    for (int k = 0; k < b; k++) {
+        int piv = k;
+        for (int r = k + 1; r < b; r++)
+            if (cabs(M[r * b + k]) > cabs(M[piv * b + k])) piv = r;
+        if (M[piv * b + k] == 0.0) return -1;
+        for (int c = 0; c < b; c++) {
+            cplx t = M[k * b + c];
+            M[k * b + c] = M[piv * b + c];
+            M[piv * b + c] = t;
+            t = Minv[k * b + c];
+            Minv[k * b + c] = Minv[piv * b + c];
+            Minv[piv * b + c] = t;
+        }
+        const cplx d = M[k * b + k];
+        for (int c = 0; c < b; c++) {
+            M[k * b + c] /= d;
+            Minv[k * b + c] /= d;
+        }
+        for (int r = 0; r < b; r++) {
+            if (r == k) continue;
+            const cplx f = M[r * b + k];
+            for (int c = 0; c < b; c++) {
+                M[r * b + c] -= f * M[k * b + c];
+                Minv[r * b + c] -= f * Minv[k * b + c];
+            }
+        }
+    }
+    return 0;
+}
+
+/* C = A B for complex b x b blocks. */
+static void mul_cplx(int b, const cplx *A, const cplx *B, cplx *C)
+{
+    for (int r = 0; r < b; r++)
+        for (int c = 0; c < b; c++) {
+            cplx acc = 0.0;
+            for (int t = 0; t < b; t++) acc += A[r * b + t] * B[t * b + c];
+            C[r * b + c] = acc;
+        }
+}
+
+static int find_entry(const int32_t *row_ptr, const int32_t *col_idx, int i, int j)
+{
+    for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++)
+        if (col_idx[p] == j) return p;
+    return -1;
+}
+
+/* Block ILU(0) of the matrix of one system -- the paper's implicit smoother
+ * (Generalized RK scheme: "ILU(0)" approximate inversion of the LHS) -- in the
+ * elimination order given by rank[] (rank[i] = position of node i), by the
+ * row-oriented (IKJ) elimination restricted to the sparsity pattern:
+ *
+ *   for every row i in order, for every neighbour k of i earlier in the
+ *   order (by increasing rank):
+ *       L_ik = W_ik U_kk^-1,
+ *       W_ij -= L_ik U_kj  for every j later than k in row k with (i, j) in the
+ *                          pattern (j = i: the diagonal block),
+ *
+ * W starting as the system's matrix: A_ii = J_ii + (D_i + i omega V_i) I and
+ * A_ij = J_ij e^{i side sigma} (phase-lagged periodic entries), with every
+ * coupling between partitions dropped (part != NULL).  Out (interleaved
+ * complex): Fdiag [n][b][b] = U_ii, Foffd [nnz][b][b] = L_ij (j earlier) or
+ * U_ij (j later), zero for dropped entries.  Returns -1 on a zero pivot. */
+int oracle_ilu_factor(int n, int b, const int32_t *row_ptr, const int32_t *col_idx, const double *offd,
+                      const double *diag, const double *D, const double *vol, double omega,
+                      const int8_t *side, double sigma, const int32_t *part, const int32_t *rank,
+                      double *Fdiag, double *Foffd)
+{
+    const int bb = b * b;
+    cplx *Wd = (cplx *)Fdiag, *Wo = (cplx *)Foffd;
+    for (int i = 0; i < n; i++) {
+        for (int t = 0; t < bb; t++) Wd[(size_t)i * bb + t] = diag[(size_t)i * bb + t];
+        for (int r = 0; r < b; r++) Wd[(size_t)i * bb + r * b + r] += D[i] + I * omega * vol[i];
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
+            const int j = col_idx[p];
+            const int drop = part && part[i] != part[j];
+            const cplx ph = (side && side[p]) ? cexp(I * (double)side[p] * sigma) : 1.0;
+            for (int t = 0; t < bb; t++) Wo[(size_t)p * bb + t] = drop ? 0.0 : ph * offd[(size_t)p * bb + t];
+        }
+    }
+    int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; i++) perm[rank[i]] = i;
+    cplx Uinv[MAXB * MAXB], tmp[MAXB * MAXB], L[MAXB * MAXB], upd[MAXB * MAXB];
+    int fail = 0;
+    for (int pos = 0; pos < n; pos++) {
+        const int i = perm[pos];
+        /* earlier neighbours of i, by increasing rank */
+        int lower[64], nl = 0;
+        for (int p = row_ptr[i]; p < row_ptr[i + 1] && nl < 64; p++) {
+            const int k = col_idx[p];
+            if (rank[k] < rank[i] && !(part && part[k] != part[i])) lower[nl++] = p;
+        }
+        for (int a = 1; a < nl; a++)
+            for (int c = a; c > 0 && rank[col_idx[lower[c]]] < rank[col_idx[lower[c - 1]]]; c--) {
+                int t = lower[c];
+                lower[c] = lower[c - 1];
+                lower[c - 1] = t;
+            }
+        for (int a = 0; a < nl; a++) {
+            const int pik = lower[a], k = col_idx[pik];
+            for (int t = 0; t < bb; t++) tmp[t] = Wd[(size_t)k * bb + t];
+            if (inv_cplx(b, tmp, Uinv)) fail = 1;
+            mul_cplx(b, Wo + (size_t)pik * bb, Uinv, L);
+            for (int q = row_ptr[k]; q < row_ptr[k + 1]; q++) {
+                const int j = col_idx[q];
+                if (rank[j] <= rank[k] || (part && part[j] != part[k])) continue;
+                cplx *target = NULL;
+                if (j == i) {
+                    target = Wd + (size_t)i * bb;
+                } else {
+                    const int pij = find_entry(row_ptr, col_idx, i, j);
+                    if (pij >= 0 && !(part && part[j] != part[i])) target = Wo + (size_t)pij * bb;
+                }
+                if (!target) continue; /* fill outside the pattern: dropped */
+                mul_cplx(b, L, Wo + (size_t)q * bb, upd);
+                for (int t = 0; t < bb; t++) target[t] -= upd[t];
+            }
+            for (int t = 0; t < bb; t++) Wo[(size_t)pik * bb + t] = L[t];
+        }
+    }
+    free(perm);
+    return fail ? -1 : 0;
+}
+
+/* y = (L U)^-1 r for the factors of oracle_ilu_factor (unit lower L):
+ * forward z_i = r_i - sum_{k earlier} L_ik z_k, then backward
+ * y_i = U_ii^-1 (z_i - sum_{j later} U_ij y_j), both in rank order.
+ * r, y: interleaved complex [n][b]. */
+int oracle_ilu_apply(int n, int b, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *part,
+                     const int32_t *rank, const double *Fdiag, const double *Foffd, const double *r, double *y)
+{
+    const int bb = b * b;
+    const cplx *Ud = (const cplx *)Fdiag, *Fo = (const cplx *)Foffd;
+    cplx *z = (cplx *)y;
+    const cplx *rc = (const cplx *)r;
+    int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; i++) perm[rank[i]] = i;
+    for (int t = 0; t < n * b; t++) z[t] = rc[t];
+    for (int pos = 0; pos < n; pos++) {
+        const int i = perm[pos];
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
+            const int k = col_idx[p];
+            if (rank[k] >= rank[i] || (part && part[k] != part[i])) continue;
+            for (int rr = 0; rr < b; rr++) {
+                cplx acc = 0.0;
+                for (int t = 0; t < b; t++) acc += Fo[(size_t)p * bb + rr * b + t] * z[(size_t)k * b + t];
+                z[(size_t)i * b + rr] -= acc;
+            }
+        }
+    }
+    int fail = 0;
+    for (int pos = n - 1; pos >= 0; pos--) {
+        const int i = perm[pos];
+        cplx t_[MAXB], M[MAXB * MAXB];
+        for (int rr = 0; rr < b; rr++) t_[rr] = z[(size_t)i * b + rr];
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; p++) {
+            const int j = col_idx[p];
+            if (rank[j] <= rank[i] || (part && part[j] != part[i])) continue;
+            for (int rr = 0; rr < b; rr++) {
+                cplx acc = 0.0;
+                for (int t = 0; t < b; t++) acc += Fo[(size_t)p * bb + rr * b + t] * z[(size_t)j * b + t];
+                t_[rr] -= acc;
+            }
+        }
+        for (int t = 0; t < bb; t++) M[t] = Ud[(size_t)i * bb + t];
+        if (lu_solve_cplx(b, M, t_)) fail = 1;
+        for (int rr = 0; rr < b; rr++) z[(size_t)i * b + rr] = t_[rr];
+    }
+    free(perm);
+    return fail ? -1 : 0;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

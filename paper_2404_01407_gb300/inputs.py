@@ -139,6 +139,15 @@ def box_partition(dims, parts) -> np.ndarray:
     return np.ascontiguousarray((bi + px * (bj + py * bk)).ravel(), dtype=np.int32)
 
 
+def lattice_colors(dims) -> np.ndarray:
+    """Red-black colouring of an nx*ny*nz lattice, (i + j + k) mod 2: no two
+    lattice neighbours share a colour (nor, for even ny, the two ends of a
+    pitchwise periodic edge)."""
+    nx, ny, nz = dims
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.ascontiguousarray(((i + j + k) % 2).ravel(), dtype=np.int32)
+
+
 def custom_mesh(positions, edge_nodes, vol=None) -> Mesh:
     """Mesh from explicit positions and edges (tiny hand-made cases)."""
     pos = np.asarray(positions, dtype=np.float64).reshape(-1, 3)

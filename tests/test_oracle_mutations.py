@@ -49,6 +49,13 @@ MUTATIONS = {
     "partition_cut_ignored": ("if (part && part[col_idx[p]] != part[i]) continue;", ""),
     "partition_cut_inverted": ("if (part && part[col_idx[p]] != part[i]) continue;",
                                "if (part && part[col_idx[p]] == part[i]) continue;"),
+    "ilu_multiplier_order": ("mul_cplx(b, Wo + (size_t)pik * bb, Uinv, L);", "mul_cplx(b, Uinv, Wo + (size_t)pik * bb, L);"),
+    "ilu_update_sign": ("for (int t = 0; t < bb; t++) target[t] -= upd[t];",
+                        "for (int t = 0; t < bb; t++) target[t] += upd[t];"),
+    "ilu_update_from_lower_row_part": ("if (rank[j] <= rank[k] || (part && part[j] != part[k])) continue;",
+                                       "if (part && part[j] != part[k]) continue;"),
+    "ilu_forward_uses_upper": ("if (rank[k] >= rank[i] || (part && part[k] != part[i])) continue;",
+                               "if (rank[k] <= rank[i] || (part && part[k] != part[i])) continue;"),
     "sylvester_wrong_index": ("double am = A[t * b + c] - ((t == c) ? lam[m] : 0.0);",
                               "double am = A[c * b + t] - ((t == c) ? lam[m] : 0.0);"),
 }

@@ -24,6 +24,12 @@ paper or by mathematics:
   behaves exactly like a ring of P identical passages joined by plain
   periodic edges whose right-hand side advances by e^{i sigma} per passage --
   sweep by sweep for Jacobi, and entry by entry for the residual.
+* Block ILU(0) (the paper's implicit smoother): (L U)_ij = A_ij on every block
+  of the pattern (hexahedral and triangulated patterns, red-black and natural
+  orders), fill outside the pattern dropped, exact LU on a chain, on
+  triangle-free patterns only the pivots change, partitions factor apart,
+  iterations converge to the direct solve, and the phase-lagged passage
+  equals the ring of passages iteration by iteration.
 * Domain truncation (couplings across partitions dropped in the sweep): one
   partition is plain Jacobi, bit for bit; converged truncated Jacobi equals
   independent dense solves of every partition's diagonal sub-matrix; with
@@ -600,3 +606,160 @@ def test_single_node_partitions_fix_after_one_sweep():
         M = jac.diag[i] + (jac.D[i] + 1j * om[0] * mesh.vol[i]) * np.eye(b)
         y = np.linalg.solve(M, B[i, 1] + 1j * B[i, 2])
         assert np.allclose(X1[i, 1] + 1j * X1[i, 2], y, rtol=1e-13, atol=1e-14 * np.abs(y).max())
+
+
+# ------------------------------------------------------------------ ILU(0)
+
+def _dense_lu(jac, rank, Fd, Fo, part=None):
+    """Dense unit-lower L and upper U from the block factors."""
+    n, b = Fd.shape[0], Fd.shape[1]
+    L = np.eye(n * b, dtype=np.complex128)
+    U = np.zeros((n * b, n * b), dtype=np.complex128)
+    for i in range(n):
+        U[i * b:(i + 1) * b, i * b:(i + 1) * b] = Fd[i]
+        for p in range(jac.row_ptr[i], jac.row_ptr[i + 1]):
+            j = jac.col_idx[p]
+            if part is not None and part[i] != part[j]:
+                continue
+            tgt = L if rank[j] < rank[i] else U
+            tgt[i * b:(i + 1) * b, j * b:(j + 1) * b] = Fo[p]
+    return L, U
+
+
+def _pattern_mask(jac, n, b, part=None):
+    M = np.zeros((n * b, n * b), dtype=bool)
+    for i in range(n):
+        M[i * b:(i + 1) * b, i * b:(i + 1) * b] = True
+        for p in range(jac.row_ptr[i], jac.row_ptr[i + 1]):
+            j = jac.col_idx[p]
+            if part is None or part[i] == part[j]:
+                M[i * b:(i + 1) * b, j * b:(j + 1) * b] = True
+    return M
+
+
+def _mesh_with_triangles():
+    """A 4x3x2 lattice plus one diagonal per xy cell: every cell holds triangles."""
+    base = inputs.hex_mesh(4, 3, 2, seed=31)
+    nx, ny = 4, 3
+    extra = []
+    for k in range(2):
+        for j in range(ny - 1):
+            for i in range(nx - 1):
+                extra.append((i + nx * (j + ny * k), i + 1 + nx * (j + 1 + ny * k)))
+    en = np.concatenate([base.edge_nodes, np.array(extra, dtype=np.int32)])
+    return inputs.custom_mesh(base.positions, en, vol=base.vol)
+
+
+@pytest.mark.parametrize("case", ["hex_redblack", "hex_natural", "triangles_greedy"])
+def test_ilu0_reproduces_the_matrix_on_its_pattern(case):
+    """ILU(0) defining property: (L U)_ij = A_ij on every block of the pattern."""
+    if case.startswith("hex"):
+        mesh = inputs.hex_mesh(4, 3, 3, seed=1)
+        color = inputs.lattice_colors((4, 3, 3)) if case == "hex_redblack" else np.zeros(mesh.n_nodes)
+        rank = oracle.elimination_rank(color) if case == "hex_redblack" else np.arange(mesh.n_nodes, dtype=np.int32)
+    else:
+        mesh = _mesh_with_triangles()
+        rank = oracle.elimination_rank(np.arange(mesh.n_nodes) % 3)
+    q = inputs.flow_state(mesh.n_nodes, 5, seed=2)
+    jac = oracle.build_jacobian(mesh.n_nodes, mesh.edge_nodes, mesh.normals, q, 15.0)
+    n, b = mesh.n_nodes, 5
+    for w in (0.0, 1.7):
+        Fd, Fo = oracle.ilu_factor(jac, mesh.vol, w, rank)
+        L, U = _dense_lu(jac, rank, Fd, Fo)
+        A = _dense.dense_operator(jac.row_ptr, jac.col_idx, jac.offd, jac.diag, jac.D, mesh.vol, w)
+        M = _pattern_mask(jac, n, b)
+        LU = L @ U
+        assert np.abs((LU - A)[M]).max() <= 1e-12 * np.abs(A).max()
+        if case == "triangles_greedy":
+            # not an exact factorisation: fill outside the pattern was dropped
+            assert np.abs((LU - A)[~M]).max() > 1e-6 * np.abs(A).max()
+
+
+def test_ilu0_on_triangle_free_pattern_only_changes_pivots():
+    """No triangles: the upper blocks stay A_ij and L_ik = A_ik U_kk^-1."""
+    mesh = inputs.hex_mesh(5, 4, 3, seed=3)
+    q = inputs.flow_state(mesh.n_nodes, 6, seed=4)
+    jac = oracle.build_jacobian(mesh.n_nodes, mesh.edge_nodes, mesh.normals, q, 20.0)
+    rank = oracle.elimination_rank(inputs.lattice_colors((5, 4, 3)))
+    Fd, Fo = oracle.ilu_factor(jac, mesh.vol, 2.0, rank)
+    owner = np.repeat(np.arange(mesh.n_nodes), np.diff(jac.row_ptr))
+    for p in range(jac.nnz):
+        i, j = owner[p], jac.col_idx[p]
+        if rank[j] > rank[i]:
+            assert np.array_equal(Fo[p], jac.offd[p].astype(np.complex128))
+        else:
+            assert np.allclose(Fo[p] @ Fd[j], jac.offd[p], rtol=0, atol=1e-12 * np.abs(jac.offd[p]).max())
+
+
+def test_ilu0_is_exact_on_a_chain():
+    """A path graph in natural order has no fill: one application solves A x = r."""
+    n = 7
+    pos = np.stack([np.arange(n, dtype=float), np.zeros(n), np.zeros(n)], axis=1)
+    pos[:, 1] = 0.05 * np.sin(np.arange(n))
+    mesh = inputs.custom_mesh(pos, np.stack([np.arange(n - 1), np.arange(1, n)], axis=1))
+    q = inputs.flow_state(n, 6, seed=5)
+    jac = oracle.build_jacobian(n, mesh.edge_nodes, mesh.normals, q, 5.0)
+    rank = np.arange(n, dtype=np.int32)
+    F = oracle.ilu_factor(jac, mesh.vol, 0.8, rank)
+    r = np.random.default_rng(6).normal(size=(n, 6)) + 1j * np.random.default_rng(7).normal(size=(n, 6))
+    y = oracle.ilu_apply(jac, rank, F, r)
+    A = _dense.dense_operator(jac.row_ptr, jac.col_idx, jac.offd, jac.diag, jac.D, mesh.vol, 0.8)
+    x = np.linalg.solve(A, r.ravel())
+    assert np.linalg.norm(y.ravel() - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_ilu_iteration_converges_to_direct_solve():
+    mesh, jac, B, om = small_problem(dims=(4, 4, 3), block=6, n_harm=2)
+    color = inputs.lattice_colors((4, 4, 3))
+    X = oracle.ilu_iterate(jac, mesh.vol, om, B, 40, color)
+    got = _dense.split_systems(X, len(om))
+    bs = _dense.split_systems(B, len(om))
+    for k, w in enumerate(_systems(jac, mesh.vol, om)):
+        A = _dense.dense_operator(jac.row_ptr, jac.col_idx, jac.offd, jac.diag, jac.D, mesh.vol, w)
+        xd = np.linalg.solve(A, bs[k])
+        assert np.linalg.norm(got[k] - xd) <= 1e-12 * np.linalg.norm(xd)
+
+
+def test_truncated_ilu0_factors_each_partition():
+    """With partitions, ILU(0) of the matrix without cross-partition blocks."""
+    dims = (6, 4, 3)
+    mesh = inputs.hex_mesh(*dims, seed=8)
+    q = inputs.flow_state(mesh.n_nodes, 5, seed=9)
+    jac = oracle.build_jacobian(mesh.n_nodes, mesh.edge_nodes, mesh.normals, q, 20.0)
+    part = inputs.box_partition(dims, (2, 2, 1))
+    rank = oracle.elimination_rank(inputs.lattice_colors(dims))
+    Fd, Fo = oracle.ilu_factor(jac, mesh.vol, 1.1, rank, part=part)
+    L, U = _dense_lu(jac, rank, Fd, Fo, part=part)
+    A = _dense.dense_operator(jac.row_ptr, jac.col_idx, jac.offd, jac.diag, jac.D, mesh.vol, 1.1)
+    M = _pattern_mask(jac, mesh.n_nodes, 5, part=part)
+    LU = L @ U
+    assert np.abs((LU - A)[M]).max() <= 1e-12 * np.abs(A).max()
+    # the factors never reach across partitions: L U is block diagonal by partition
+    cross = np.repeat(part, 5)[:, None] != np.repeat(part, 5)[None, :]
+    assert np.all(LU[cross] == 0.0)
+
+
+def test_phase_lagged_ilu0_matches_ring():
+    """ILU iterations on the phase-lagged passage equal them on the ring of
+    passages (red-black colouring, even pitch), iteration by iteration."""
+    mesh = inputs.hex_mesh(3, 4, 2, seed=11, periodic_y=True)
+    q = inputs.flow_state(mesh.n_nodes, 6, seed=12)
+    jac = oracle.build_jacobian(mesh.n_nodes, mesh.edge_nodes, mesh.normals, q, 20.0, periodic=mesh.periodic)
+    N = len(RING_M)
+    B = inputs.rhs(mesh.n_nodes, 6, N, seed=13)
+    om = inputs.omegas(N, 0.9)
+    sigma = 2.0 * np.pi * np.asarray(RING_M, dtype=np.float64) / RING_P
+    P = RING_P
+    n = mesh.n_nodes
+    ren, rnorm, rvol, rq = ring_of_passages(mesh, q, P)
+    rjac = oracle.build_jacobian(n * P, ren, rnorm, rq, 20.0)
+    # colour by lattice parity (the pitch 4 is even, so the periodic edges join
+    # different colours); every passage of the ring repeats the passage's
+    # colours.  Nodes of one colour never couple, so the factors depend on the
+    # colouring only, not on the order within a colour.
+    color = inputs.lattice_colors((3, 4, 2))
+    rcolor = np.tile(color, P)
+    got = oracle.ilu_iterate(jac, mesh.vol, om, B, 3, color, sigma=sigma)
+    ring = oracle.ilu_iterate(rjac, rvol, om, phase_shift(B, N, sigma, P), 3, rcolor)
+    ref = phase_shift(got, N, sigma, P)
+    assert np.allclose(ring, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
