@@ -346,6 +346,8 @@ def run_fnlh(args):
         line["periodic"] = periodic_section(torch, fnlh, inputs, dev)
         torch.cuda.empty_cache()
         line["partitions"] = partition_section(torch, fnlh, inputs, dev)
+        torch.cuda.empty_cache()
+        line["ilu_vs_jacobi"] = ilu_section(torch, fnlh, inputs, dev)
         if not args.no_large:
             torch.cuda.empty_cache()
             line["large"] = large_section(torch, fnlh, inputs, dev)
@@ -473,6 +475,52 @@ def periodic_section(torch, fnlh, inputs, dev):
         torch.cuda.empty_cache()
     for name in ("f64", "f32", "bf16"):
         out[f"{name}_overhead"] = out["periodic"][f"{name}_sweep_ms"] / out["plain"][f"{name}_sweep_ms"] - 1.0
+    return out
+
+
+def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
+    """The paper's smoother, block ILU(0) in red-black order, against block
+    Jacobi on the measured passage: iterations and time to a 1e-8 FP64
+    residual, and the paper's stage rule (1e-2 drop from zero, at most 10)."""
+    p = inputs.config_problem(WORKLOAD)
+    n, b, N = p.mesh.n_nodes, p.block, p.n_harm
+    dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+    J = fnlh.DeviceJacobian(dm, b, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32, dev)
+    fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+    B = torch.from_numpy(p.b).to(dev)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(n, b, N, dev)
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    out = {"workload": f"{WORKLOAD}: mean + {N} harmonics, to {tol:g} and the paper's stage rule"}
+
+    def timed(fn):
+        fn()  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    for name, prec in (("ilu_f64", fnlh.FNLH_F64), ("ilu_f32", fnlh.FNLH_F32)):
+        ilu = fnlh.DeviceIlu(dm, b, N, precision=prec, device=dev)
+        tf, _ = timed(lambda: fnlh.fnlh_ilu_factor(dm, J, p.omega, ilu, ws=ws))
+        t, (st, its, rel) = timed(lambda: fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, tol, 200, ws=ws, flags=zg,
+                                                              raise_on_error=False))
+        _, (st2, its2, rel2) = timed(lambda: fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, 1e-2, 10, ws=ws,
+                                                                 flags=zg, raise_on_error=False))
+        out[name] = {"colors": ilu.n_colors, "factor_seconds": tf, "status": fnlh.fnlh_strerror(st),
+                     "iterations": its, "seconds": t, "max_rel_residual": float(np.max(rel)),
+                     "stage_rule_iterations": its2, "factor_bytes": int(ilu.factor.numel())}
+        del ilu
+        torch.cuda.empty_cache()
+    for name, prec, inner in (("jacobi_f64", fnlh.FNLH_F64, 10), ("jacobi_f32", fnlh.FNLH_F32, 12)):
+        t, (st, checks, sweeps, rel) = timed(lambda: fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200,
+                                                                     ws=ws, flags=zg, raise_on_error=False))
+        _, (st2, c2, sw2, rel2) = timed(lambda: fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-2, 1, 11,
+                                                                ws=ws, flags=zg, raise_on_error=False))
+        out[name] = {"status": fnlh.fnlh_strerror(st), "sweeps": sweeps, "seconds": t,
+                     "max_rel_residual": float(np.max(rel)), "stage_rule_sweeps": sw2,
+                     "stage_rule_status": fnlh.fnlh_strerror(st2)}
     return out
 
 

@@ -288,6 +288,72 @@ int fnlh_residual_noalloc(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t
                           const double *omega, const double *sigma, const double *B,
                           const double *X, double *r, double *norms, fnlh_stream_t stream);
 
+/* ------------------------------------------------------------------ ILU(0)
+ *
+ * The paper's implicit smoother ("Generalized RK Scheme": the LHS of every
+ * stage is inverted approximately by ILU(0) iterations, each partition of a
+ * parallel run factored on its own).  Here block ILU(0) in multicolour order:
+ * the nodes are grouped by colour (no two neighbours share one), so each
+ * triangular solve is a sequence of parallel colour passes.  On a pattern
+ * without triangles (three pairwise adjacent nodes; hexahedral edge graphs
+ * have none) elimination changes only the pivot blocks,
+ *     P_i = A_ii - sum_{j of an earlier colour} A_ij P_j^-1 A_ji,
+ * with L_ij = A_ij P_j^-1 and U_ij = A_ij, so the factor is one inverse pivot
+ * block per node and system and J supplies every off-diagonal block.  A_ij
+ * carries the phase-lag factor on periodic entries (the pivots do not depend
+ * on it: an edge's two couplings carry opposite phases) and is dropped
+ * between partitions (`part`). */
+
+/* HOST helper: greedy colouring of the neighbour graph in node order (each
+ * node takes the smallest colour none of its earlier neighbours has), and the
+ * nodes grouped by colour: order[color_ptr[c] .. color_ptr[c+1]) are the nodes
+ * of colour c, ascending.  row_ptr/col_idx: host CSR (untagged); color, order
+ * [n]; color_ptr [max_colors + 1].  FNLH_ERR_UNSUPPORTED if more than
+ * max_colors colours are needed. */
+int fnlh_mesh_color(int32_t n_nodes, const int32_t *row_ptr, const int32_t *col_idx, int32_t max_colors,
+                    int32_t *color, int32_t *order, int32_t *color_ptr, int32_t *n_colors);
+
+typedef struct fnlh_ilu {
+    int32_t n_colors;
+    const int32_t *color;     /* [n] device: colour of every node */
+    const int32_t *order;     /* [n] device: nodes grouped by colour, colour 0 first */
+    const int32_t *color_ptr; /* HOST [n_colors + 1]: order[color_ptr[c] .. color_ptr[c+1]) have colour c */
+    void *factor;             /* device, fnlh_ilu_bytes(n, b, n_harm, precision) bytes */
+    size_t factor_bytes;
+    int32_t precision;        /* FNLH_F64: FP64 factor and iterations; FNLH_F32: FP32 factor and
+                                 correction passes (pivots formed in FP64 from the stored FP32
+                                 inverses of earlier colours), FP64 residual and update */
+    int32_t n_harm;           /* systems the factor holds (set by fnlh_ilu_factor) */
+    int32_t ready;            /* set to 1 by fnlh_ilu_factor */
+} fnlh_ilu;
+
+/* Bytes of the factor: n (1 + n_harm) b^2 complex values of the precision. */
+size_t fnlh_ilu_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision);
+
+/* Factor every system (omega: HOST [n_harm]) into ilu->factor.  Uses J's FP64
+ * blocks in the original basis (no prep needed, except FNLH_PREP_TAGS on a
+ * mesh with periodic edges or partitions).  SYNCHRONISING: first checks on the
+ * device that neighbours have different colours and `order` groups every node
+ * once by colour (FNLH_ERR_BAD_MESH), and that the pattern, without the
+ * couplings between partitions, has no triangle (FNLH_ERR_UNSUPPORTED: block
+ * ILU(0) would then need off-diagonal factors); FNLH_ERR_NONFINITE on a
+ * singular pivot.  workspace: fnlh_workspace_bytes(n, b, n_harm, FNLH_F64). */
+int fnlh_ilu_factor(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, const double *omega,
+                    fnlh_ilu *ilu, void *workspace, size_t workspace_bytes, fnlh_stream_t stream);
+
+/* ILU(0) iterations x <- x + (L U)^-1 (B - A x) on every system with the
+ * factor of fnlh_ilu_factor (same n_harm and omega); the FP64 residual keeps
+ * every coupling.  Before each iteration ||B_k - A_k x_k|| <= tol ||B_k|| for
+ * all k ends the solve (with x0 = 0 and tol = 1e-2, max_iterations = 10: the
+ * paper's rule).  flags: FNLH_SOLVE_ZERO_GUESS, FNLH_SOLVE_MASK_CONVERGED.
+ * SYNCHRONISING.  Outputs (host, nullable): *iterations_done, rel_res [K].
+ * Returns FNLH_ERR_NOT_CONVERGED after max_iterations, FNLH_ERR_NONFINITE /
+ * FNLH_ERR_DIVERGED as fnlh_solve.  workspace: the FNLH_F64 size. */
+int fnlh_solve_ilu(const fnlh_mesh *mesh, const fnlh_jacobian *J, const fnlh_ilu *ilu, int32_t n_harm,
+                   const double *omega, const double *sigma, const double *B, double *X, double tol,
+                   int32_t max_iterations, int32_t flags, void *workspace, size_t workspace_bytes,
+                   int32_t *iterations_done, double *rel_res, fnlh_stream_t stream);
+
 /* Timing hook (not part of the paper): when both are non-NULL, every later
  * relaxation on this host thread records `begin` on its stream right before
  * its first sweep launch and `end` right after its last one, so that the

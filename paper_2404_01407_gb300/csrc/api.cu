@@ -24,6 +24,9 @@ size_t batched_extra_bytes(int n_rows);
 void set_sweep_events(cudaEvent_t b, cudaEvent_t e);
 int residual_noalloc_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*,
                             double*, double*, cudaStream_t);
+int ilu_factor_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, fnlh_ilu*, void*, cudaStream_t);
+int solve_ilu_impl(const fnlh_mesh*, const fnlh_jacobian*, const fnlh_ilu*, int, const double*, const double*,
+                   const double*, double*, double, int, int, void*, int*, double*, cudaStream_t);
 }  // namespace fnlh
 
 using namespace fnlh;
@@ -284,6 +287,91 @@ int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t
   if (!norms || (mesh->n_nodes > 0 && (!B || !X))) return FNLH_ERR_ARG;
   const Systems sys = make_systems(n_harm, omega, sigma);
   return residual_noalloc_launch(mesh, J, sys, B, X, r, norms, (cudaStream_t)stream);
+}
+
+int fnlh_mesh_color(int32_t n_nodes, const int32_t* row_ptr, const int32_t* col_idx, int32_t max_colors,
+                    int32_t* color, int32_t* order, int32_t* color_ptr, int32_t* n_colors) {
+  if (n_nodes < 0 || max_colors < 1 || !row_ptr || !color || !order || !color_ptr || !n_colors) return FNLH_ERR_ARG;
+  if (n_nodes > 0 && row_ptr[n_nodes] > 0 && !col_idx) return FNLH_ERR_ARG;
+  std::vector<int32_t> used((size_t)max_colors + 1, -1);
+  int32_t top = 0;
+  for (int32_t i = 0; i < n_nodes; ++i) {
+    for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+      const int32_t j = col_idx[p];
+      if (j < 0 || j >= n_nodes) return FNLH_ERR_BAD_MESH;
+      if (j < i && color[j] < max_colors) used[color[j]] = i;
+    }
+    int32_t c = 0;
+    while (c < max_colors && used[c] == i) ++c;
+    if (c >= max_colors) return FNLH_ERR_UNSUPPORTED;
+    color[i] = c;
+    top = std::max(top, c + 1);
+  }
+  *n_colors = top;
+  for (int32_t c = 0; c <= top; ++c) color_ptr[c] = 0;
+  for (int32_t i = 0; i < n_nodes; ++i) color_ptr[color[i] + 1]++;
+  for (int32_t c = 0; c < top; ++c) color_ptr[c + 1] += color_ptr[c];
+  std::vector<int32_t> fill(color_ptr, color_ptr + top + 1);
+  for (int32_t i = 0; i < n_nodes; ++i) order[fill[color[i]]++] = i;
+  return FNLH_OK;
+}
+
+size_t fnlh_ilu_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision) {
+  if (n_nodes < 0 || (block != 5 && block != 6) || n_harm < 0 || n_harm > FNLH_MAX_HARMONICS) return 0;
+  if (precision != FNLH_F64 && precision != FNLH_F32) return 0;
+  const size_t elem = precision == FNLH_F64 ? 8 : 4;
+  return (size_t)n_nodes * (1 + (size_t)n_harm) * block * block * 2 * elem;
+}
+
+static int check_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_ilu* ilu, int n_harm) {
+  if (!ilu) return FNLH_ERR_ARG;
+  if (ilu->precision != FNLH_F64 && ilu->precision != FNLH_F32) return FNLH_ERR_ARG;
+  if (ilu->n_colors < 1 && mesh->n_nodes > 0) return FNLH_ERR_ARG;
+  if (mesh->n_nodes > 0 && (!ilu->color || !ilu->order || !ilu->color_ptr || !ilu->factor)) return FNLH_ERR_ARG;
+  if (!aligned(ilu->factor, 16)) return FNLH_ERR_ARG;
+  if (ilu->factor_bytes < fnlh_ilu_bytes(mesh->n_nodes, J->block, n_harm, ilu->precision)) return FNLH_ERR_WORKSPACE;
+  for (int c = 0; c < ilu->n_colors; ++c)
+    if (ilu->color_ptr[c] > ilu->color_ptr[c + 1]) return FNLH_ERR_ARG;
+  if (mesh->n_nodes > 0 && (ilu->color_ptr[0] != 0 || ilu->color_ptr[ilu->n_colors] != mesh->n_nodes))
+    return FNLH_ERR_ARG;
+  return FNLH_OK;
+}
+
+int fnlh_ilu_factor(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega, fnlh_ilu* ilu,
+                    void* workspace, size_t workspace_bytes, fnlh_stream_t stream) {
+  FNLH_TRY(check_mesh(mesh, false));
+  FNLH_TRY(check_jac(mesh, J));
+  FNLH_TRY(check_systems(n_harm, omega, nullptr));
+  FNLH_TRY(check_tags(mesh, J));
+  FNLH_TRY(check_ilu(mesh, J, ilu, n_harm));
+  FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, FNLH_F64));
+  FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
+  ilu->ready = 0;
+  if (mesh->n_nodes == 0) {
+    ilu->n_harm = n_harm;
+    ilu->ready = 1;
+    return FNLH_OK;
+  }
+  return ilu_factor_impl(mesh, J, n_harm, omega, ilu, workspace, (cudaStream_t)stream);
+}
+
+int fnlh_solve_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_ilu* ilu, int32_t n_harm,
+                   const double* omega, const double* sigma, const double* B, double* X, double tol,
+                   int32_t max_iterations, int32_t flags, void* workspace, size_t workspace_bytes,
+                   int32_t* iterations_done, double* rel_res, fnlh_stream_t stream) {
+  FNLH_TRY(check_mesh(mesh, false));
+  FNLH_TRY(check_jac(mesh, J));
+  FNLH_TRY(check_systems(n_harm, omega, sigma));
+  FNLH_TRY(check_tags(mesh, J));
+  FNLH_TRY(check_ilu(mesh, J, ilu, n_harm));
+  if (!ilu->ready || ilu->n_harm != n_harm) return FNLH_ERR_WORKSPACE;
+  if (!(tol >= 0.0) || max_iterations < 0) return FNLH_ERR_ARG;
+  if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
+  if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;
+  FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, FNLH_F64));
+  FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
+  return solve_ilu_impl(mesh, J, ilu, n_harm, omega, sigma, B, X, tol, max_iterations, flags, workspace,
+                        iterations_done, rel_res, (cudaStream_t)stream);
 }
 
 int fnlh_set_sweep_events(void* begin, void* end) {

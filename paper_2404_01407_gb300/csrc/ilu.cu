@@ -1,0 +1,541 @@
+// Block ILU(0) smoother in multicolour order.
+//
+// Paper: arXiv 2404.01407, "Generalized RK Scheme" -- the implicit LHS of
+// every RK stage (mean flow and each harmonic, Eq. lhs_mean / Eq. lhs_lin) is
+// inverted approximately by ILU(0) iterations, stopped by the linear-residual
+// rule of Table fnlh_para; on a parallel run each partition is factored on its
+// own (the couplings between partitions are ignored).
+//
+// Design (GB300): the nodes are ordered by colour (no two neighbours share a
+// colour), so every triangular solve is a short sequence of fully parallel
+// colour passes.  On a pattern without triangles (three pairwise adjacent
+// nodes -- none in a hexahedral edge graph) block ILU(0) changes only the
+// pivot blocks: with P_i = A_ii - sum_{j earlier} A_ij P_j^-1 A_ji the factors
+// are L_ij = A_ij P_j^-1 and U_ij = A_ij, so the library stores just P_i^-1
+// per node and system, and the shared J supplies every off-diagonal block.
+// One iteration x <- x + (LU)^-1 r, r = B - A x (FP64, every coupling):
+//   forward, colours ascending:   z_i = P_i^-1 (r_i - sum_{j earlier} A_ij z_j)
+//   backward, colours descending: y_i = z_i - P_i^-1 sum_{j later} A_ij y_j,
+//                                 x_i += y_i
+// with A_ij carrying the phase-lag factor of periodic entries.  An edge's two
+// couplings carry opposite phases, so the pivots do not depend on them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fnlh {
+
+constexpr int kIluThreads = 128;
+constexpr int kPivotThreads = 32;
+
+int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
+                    const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
+                    cudaStream_t s);
+Systems make_systems(int n_harm, const double* omega, const double* sigma);
+
+// ------------------------------------------------------------- validation
+
+// Bit 0: two neighbours share a colour or a colour is out of range; bit 1: the
+// (truncated) pattern has a triangle; bit 2: `order` is not a permutation
+// grouped by colour.
+__global__ void k_ilu_check_graph(int32_t n, int32_t n_colors, const int32_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ cols, const int32_t* __restrict__ color,
+                                  int32_t* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int ci = color[i];
+  int f = (ci < 0 || ci >= n_colors) ? 1 : 0;
+  const int p0 = row_ptr[i], p1 = row_ptr[i + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int c = cols[p];
+    if (cut_of(c)) continue;
+    const int j = col_of(c);
+    if (color[j] == ci) f |= 1;
+    if (j < i) continue;  // each edge once
+    for (int q = row_ptr[j]; q < row_ptr[j + 1]; ++q) {
+      const int d = cols[q];
+      if (cut_of(d)) continue;
+      const int k = col_of(d);
+      if (k == i) continue;
+      for (int t = p0; t < p1; ++t)
+        if (!cut_of(cols[t]) && col_of(cols[t]) == k) f |= 2;
+    }
+  }
+  if (f) atomicOr(flags, f);
+}
+
+// Counts the appearances of every node in order[begin, end) and checks their colour.
+__global__ void k_ilu_check_order(int32_t n, int32_t begin, int32_t end, int32_t c, const int32_t* __restrict__ order,
+                                  const int32_t* __restrict__ color, int32_t* __restrict__ seen,
+                                  int32_t* __restrict__ flags) {
+  const int t = begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= end) return;
+  const int i = order[t];
+  if (i < 0 || i >= n || color[i] != c) {
+    atomicOr(flags, 4);
+    return;
+  }
+  atomicAdd(seen + i, 1);
+}
+
+__global__ void k_ilu_check_seen(int32_t n, const int32_t* __restrict__ seen, int32_t* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && seen[i] != 1) atomicOr(flags, 4);
+}
+
+// -------------------------------------------------------------- factor
+
+struct IluArgs {
+  int32_t n, K, begin, end;
+  const int32_t* order;
+  const int32_t* color;
+  const int32_t* row_ptr;
+  const int32_t* cols;  // tagged column indices (col_of / side_of / cut_of)
+  const double* offd;   // J_ij, original basis
+  const double* diag;
+  const double* D;
+  const double* vol;
+  void* factor;         // [n][K][b][b] complex inverse pivots (T)
+  const double* r;      // [n][C][b] residual, caller layout
+  void* E;              // [n][K][b] complex work vector (T)
+  double* X;            // [n][C][b] iterate, caller layout
+  int32_t* status;      // bit 1: a zero pivot
+  int32_t masked;
+  uint64_t active[2];
+  Systems sys;
+};
+
+__device__ __forceinline__ bool ilu_active(const IluArgs& a, int k) {
+  return !a.masked || ((a.active[k >> 6] >> (k & 63)) & 1ull);
+}
+
+// Position of column i in row j (the transposed coupling), -1 if absent.
+__device__ __forceinline__ int find_in_row(const int32_t* row_ptr, const int32_t* cols, int j, int i) {
+  for (int q = row_ptr[j]; q < row_ptr[j + 1]; ++q)
+    if (col_of(cols[q]) == i) return q;
+  return -1;
+}
+
+// Pivot blocks of the nodes of one colour, thread per (node, system): P in
+// shared memory (complex, row-major), updated by every earlier-coloured
+// neighbour j with  P -= A_ij P_j^-1 A_ji  one row at a time, then inverted by
+// Gauss-Jordan elimination with partial pivoting.
+template <int BS, typename T>
+__global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_constant__ IluArgs a) {
+  __shared__ double sP[kPivotThreads][2 * BS * BS];
+  __shared__ double sV[kPivotThreads][2 * BS * BS];
+  const int t = a.begin + blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (t >= a.end) return;
+  const int i = a.order[t];
+  double* P = sP[threadIdx.x];
+  double* V = sV[threadIdx.x];
+  const double shift_re = a.D[i], shift_im = a.sys.omega[k] * a.vol[i];
+  for (int e = 0; e < BS * BS; ++e) {
+    P[2 * e] = a.diag[(size_t)i * BS * BS + e];
+    P[2 * e + 1] = 0.0;
+  }
+  for (int r = 0; r < BS; ++r) {
+    P[2 * (r * BS + r)] += shift_re;
+    P[2 * (r * BS + r) + 1] += shift_im;
+  }
+  const int ci = a.color[i];
+  for (int p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) {
+    const int c = a.cols[p];
+    if (cut_of(c)) continue;
+    const int j = col_of(c);
+    if (a.color[j] >= ci) continue;
+    const int q = find_in_row(a.row_ptr, a.cols, j, i);
+    if (q < 0) continue;  // not reached on a symmetric pattern
+    const double* Aij = a.offd + (size_t)p * BS * BS;
+    const double* Aji = a.offd + (size_t)q * BS * BS;
+    const T* Pj = (const T*)a.factor + ((size_t)j * a.K + k) * 2 * BS * BS;
+    for (int r = 0; r < BS; ++r) {
+      double wr[BS], wi[BS];  // row r of A_ij P_j^-1
+      for (int cc = 0; cc < BS; ++cc) {
+        double sr = 0.0, si = 0.0;
+        for (int u = 0; u < BS; ++u) {
+          const double av = Aij[r * BS + u];
+          sr += av * (double)Pj[2 * (u * BS + cc)];
+          si += av * (double)Pj[2 * (u * BS + cc) + 1];
+        }
+        wr[cc] = sr;
+        wi[cc] = si;
+      }
+      for (int cc = 0; cc < BS; ++cc) {
+        double sr = 0.0, si = 0.0;
+        for (int u = 0; u < BS; ++u) {
+          const double av = Aji[u * BS + cc];
+          sr += wr[u] * av;
+          si += wi[u] * av;
+        }
+        P[2 * (r * BS + cc)] -= sr;
+        P[2 * (r * BS + cc) + 1] -= si;
+      }
+    }
+  }
+  // V = P^-1 by Gauss-Jordan elimination with partial pivoting (|.|^2 compare)
+  for (int e = 0; e < BS * BS; ++e) {
+    V[2 * e] = (e / BS == e % BS) ? 1.0 : 0.0;
+    V[2 * e + 1] = 0.0;
+  }
+  bool ok = true;
+  for (int col = 0; col < BS; ++col) {
+    int piv = col;
+    double best = P[2 * (col * BS + col)] * P[2 * (col * BS + col)] +
+                  P[2 * (col * BS + col) + 1] * P[2 * (col * BS + col) + 1];
+    for (int r = col + 1; r < BS; ++r) {
+      const double m2 = P[2 * (r * BS + col)] * P[2 * (r * BS + col)] + P[2 * (r * BS + col) + 1] * P[2 * (r * BS + col) + 1];
+      if (m2 > best) {
+        best = m2;
+        piv = r;
+      }
+    }
+    if (!(best > 0.0)) {
+      ok = false;
+      break;
+    }
+    if (piv != col)
+      for (int cc = 0; cc < BS; ++cc)
+        for (int h = 0; h < 2; ++h) {
+          double tp = P[2 * (col * BS + cc) + h];
+          P[2 * (col * BS + cc) + h] = P[2 * (piv * BS + cc) + h];
+          P[2 * (piv * BS + cc) + h] = tp;
+          tp = V[2 * (col * BS + cc) + h];
+          V[2 * (col * BS + cc) + h] = V[2 * (piv * BS + cc) + h];
+          V[2 * (piv * BS + cc) + h] = tp;
+        }
+    // scale the pivot row by 1 / p
+    const double pr = P[2 * (col * BS + col)], pi = P[2 * (col * BS + col) + 1];
+    const double inv = 1.0 / (pr * pr + pi * pi);
+    const double qr = pr * inv, qi = -pi * inv;
+    for (int cc = 0; cc < BS; ++cc) {
+      double xr = P[2 * (col * BS + cc)], xi = P[2 * (col * BS + cc) + 1];
+      P[2 * (col * BS + cc)] = xr * qr - xi * qi;
+      P[2 * (col * BS + cc) + 1] = xr * qi + xi * qr;
+      xr = V[2 * (col * BS + cc)];
+      xi = V[2 * (col * BS + cc) + 1];
+      V[2 * (col * BS + cc)] = xr * qr - xi * qi;
+      V[2 * (col * BS + cc) + 1] = xr * qi + xi * qr;
+    }
+    for (int r = 0; r < BS; ++r) {
+      if (r == col) continue;
+      const double fr = P[2 * (r * BS + col)], fi = P[2 * (r * BS + col) + 1];
+      for (int cc = 0; cc < BS; ++cc) {
+        P[2 * (r * BS + cc)] -= fr * P[2 * (col * BS + cc)] - fi * P[2 * (col * BS + cc) + 1];
+        P[2 * (r * BS + cc) + 1] -= fr * P[2 * (col * BS + cc) + 1] + fi * P[2 * (col * BS + cc)];
+        V[2 * (r * BS + cc)] -= fr * V[2 * (col * BS + cc)] - fi * V[2 * (col * BS + cc) + 1];
+        V[2 * (r * BS + cc) + 1] -= fr * V[2 * (col * BS + cc) + 1] + fi * V[2 * (col * BS + cc)];
+      }
+    }
+  }
+  if (!ok) atomicOr(a.status, 2);
+  T* out = (T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS;
+  for (int e = 0; e < 2 * BS * BS; ++e) out[e] = ok ? (T)V[e] : T(0);
+}
+
+// --------------------------------------------------------------- apply
+
+// s -= A_ij e^{i side sigma} y_j for one neighbour slice (complex, T).
+template <int BS, typename T>
+__device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int k, T (&sr)[BS], T (&si)[BS],
+                                           T sign) {
+  const int j = col_of(cj);
+  const T* yj = (const T*)a.E + ((size_t)j * a.K + k) * 2 * BS;
+  T xr[BS], xi[BS];
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    xr[t] = yj[2 * t];
+    xi[t] = yj[2 * t + 1];
+  }
+  if (side_of(cj)) phase_shift<BS, T>(xr, xi, side_of(cj), a.sys.phase[k]);
+  const double* A = a.offd + (size_t)p * BS * BS;
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    T accr = 0, acci = 0;
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      const T av = (T)__ldg(A + r * BS + t);
+      accr += av * xr[t];
+      acci += av * xi[t];
+    }
+    sr[r] += sign * accr;
+    si[r] += sign * acci;
+  }
+}
+
+// (yr, yi) = P_i^-1 (sr, si), complex.
+template <int BS, typename T>
+__device__ __forceinline__ void ilu_pivot_apply(const T* __restrict__ Pinv, const T (&sr)[BS], const T (&si)[BS],
+                                                T (&yr)[BS], T (&yi)[BS]) {
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    T ar = 0, ai = 0;
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      const T pr = Pinv[2 * (r * BS + t)], pi = Pinv[2 * (r * BS + t) + 1];
+      ar += pr * sr[t] - pi * si[t];
+      ai += pr * si[t] + pi * sr[t];
+    }
+    yr[r] = ar;
+    yi[r] = ai;
+  }
+}
+
+// Forward pass over one colour: z_i = P_i^-1 (r_i - sum_{j earlier} A_ij z_j).
+template <int BS, typename T>
+__global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_constant__ IluArgs a) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = a.begin + g / a.K;
+  const int k = (int)(g % a.K);
+  if (t >= a.end || !ilu_active(a, k)) return;
+  const int i = a.order[t];
+  const int C = a.sys.C;
+  const int c0 = (k == 0) ? 0 : 2 * k - 1;
+  T sr[BS], si[BS];
+  const double* rp = a.r + ((size_t)i * C + c0) * BS;
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    sr[q] = (T)rp[q];
+    si[q] = (k == 0) ? T(0) : (T)rp[BS + q];
+  }
+  const int ci = a.color[i];
+  for (int p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) {
+    const int cj = a.cols[p];
+    if (cut_of(cj) || a.color[col_of(cj)] >= ci) continue;
+    ilu_gather<BS, T>(a, p, cj, k, sr, si, T(-1));
+  }
+  T yr[BS], yi[BS];
+  ilu_pivot_apply<BS, T>((const T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS, sr, si, yr, yi);
+  T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    e[2 * q] = yr[q];
+    e[2 * q + 1] = yi[q];
+  }
+}
+
+// Backward pass over one colour: y_i = z_i - P_i^-1 sum_{j later} A_ij y_j,
+// then x_i += y_i (the update, in FP64, in the caller's layout).
+template <int BS, typename T>
+__global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_constant__ IluArgs a) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = a.begin + g / a.K;
+  const int k = (int)(g % a.K);
+  if (t >= a.end || !ilu_active(a, k)) return;
+  const int i = a.order[t];
+  const int ci = a.color[i];
+  T sr[BS], si[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    sr[q] = 0;
+    si[q] = 0;
+  }
+  bool any = false;
+  for (int p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) {
+    const int cj = a.cols[p];
+    if (cut_of(cj) || a.color[col_of(cj)] <= ci) continue;
+    ilu_gather<BS, T>(a, p, cj, k, sr, si, T(1));
+    any = true;
+  }
+  T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
+  T yr[BS], yi[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    yr[q] = e[2 * q];
+    yi[q] = e[2 * q + 1];
+  }
+  if (any) {
+    T dr[BS], di[BS];
+    ilu_pivot_apply<BS, T>((const T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS, sr, si, dr, di);
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      yr[q] -= dr[q];
+      yi[q] -= di[q];
+      e[2 * q] = yr[q];
+      e[2 * q + 1] = yi[q];
+    }
+  }
+  const int C = a.sys.C;
+  double* xp = a.X + ((size_t)i * C + ((k == 0) ? 0 : 2 * k - 1)) * BS;
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    xp[q] += (double)yr[q];
+    if (k > 0) xp[BS + q] += (double)yi[q];
+  }
+}
+
+// ----------------------------------------------------------------- host
+
+static inline unsigned grid_for(long long count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+static IluArgs ilu_args(const fnlh_mesh* m, const fnlh_jacobian* J, const fnlh_ilu* ilu, const Systems& sys) {
+  IluArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = m->n_nodes;
+  a.K = sys.K;
+  a.order = ilu->order;
+  a.color = ilu->color;
+  a.row_ptr = m->row_ptr;
+  a.cols = csr_columns(m, J);
+  a.offd = J->offd;
+  a.diag = J->diag;
+  a.D = J->D;
+  a.vol = m->vol;
+  a.factor = ilu->factor;
+  a.sys = sys;
+  a.active[0] = a.active[1] = ~0ull;
+  return a;
+}
+
+template <int BS, typename T>
+static int factor_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, fnlh_ilu* ilu, void* ws,
+                        cudaStream_t s) {
+  const int n = m->n_nodes;
+  const WsLayout W = ws_layout(n, BS, sys.K - 1, FNLH_F64);
+  int32_t* flags = at<int32_t>(ws, W.status);
+  int32_t* seen = at<int32_t>(ws, W.vec[0]);
+  FNLH_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
+  FNLH_CUDA_TRY(cudaMemsetAsync(seen, 0, sizeof(int32_t) * (size_t)std::max(n, 1), s));
+  IluArgs a = ilu_args(m, J, ilu, sys);
+  a.status = flags + 1;
+  if (n > 0) {
+    k_ilu_check_graph<<<grid_for(n, 128), 128, 0, s>>>(n, ilu->n_colors, m->row_ptr, a.cols, ilu->color, flags);
+    FNLH_LAUNCH_CHECK();
+    for (int c = 0; c < ilu->n_colors; ++c) {
+      const int b = ilu->color_ptr[c], e = ilu->color_ptr[c + 1];
+      if (e > b) {
+        k_ilu_check_order<<<grid_for(e - b, 128), 128, 0, s>>>(n, b, e, c, ilu->order, ilu->color, seen, flags);
+        FNLH_LAUNCH_CHECK();
+      }
+    }
+    k_ilu_check_seen<<<grid_for(n, 128), 128, 0, s>>>(n, seen, flags);
+    FNLH_LAUNCH_CHECK();
+  }
+  int32_t hflags = 0;
+  FNLH_CUDA_TRY(cudaMemcpyAsync(&hflags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hflags & (1 | 4)) return FNLH_ERR_BAD_MESH;
+  if (hflags & 2) return FNLH_ERR_UNSUPPORTED;
+  for (int c = 0; c < ilu->n_colors; ++c) {
+    a.begin = ilu->color_ptr[c];
+    a.end = ilu->color_ptr[c + 1];
+    if (a.end <= a.begin) continue;
+    dim3 grid(grid_for(a.end - a.begin, kPivotThreads), sys.K);
+    k_ilu_pivots<BS, T><<<grid, kPivotThreads, 0, s>>>(a);
+    FNLH_LAUNCH_CHECK();
+  }
+  int32_t hstatus = 0;
+  FNLH_CUDA_TRY(cudaMemcpyAsync(&hstatus, flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hstatus) return FNLH_ERR_NONFINITE;
+  ilu->n_harm = sys.K - 1;
+  ilu->ready = 1;
+  return FNLH_OK;
+}
+
+int ilu_factor_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, fnlh_ilu* ilu,
+                    void* ws, cudaStream_t s) {
+  const Systems sys = make_systems(n_harm, omega, nullptr);
+  if (J->block == 5)
+    return ilu->precision == FNLH_F64 ? factor_typed<5, double>(m, J, sys, ilu, ws, s)
+                                      : factor_typed<5, float>(m, J, sys, ilu, ws, s);
+  return ilu->precision == FNLH_F64 ? factor_typed<6, double>(m, J, sys, ilu, ws, s)
+                                    : factor_typed<6, float>(m, J, sys, ilu, ws, s);
+}
+
+struct IluCheck {
+  double rel[kMaxSys];
+  double first_max;
+};
+
+template <int BS, typename T>
+static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnlh_ilu* ilu, const Systems& sys,
+                           const double* B, double* X, double tol, int max_iterations, int flags, void* ws,
+                           int* iterations_done, double* rel_res, cudaStream_t s) {
+  const int n = m->n_nodes, K = sys.K;
+  const WsLayout W = ws_layout(n, BS, K - 1, FNLH_F64);
+  double* norms = at<double>(ws, W.norms);
+  double* r = at<double>(ws, W.vec[0]);
+  IluArgs a = ilu_args(m, J, ilu, sys);
+  a.r = r;
+  a.E = at<T>(ws, W.vec[1]);
+  a.X = X;
+  a.status = at<int32_t>(ws, W.status);
+  const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
+  bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
+  if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
+  double hn[2 * kMaxSys];
+  IluCheck ck;
+  ck.first_max = 0.0;
+  int it = 0, rc = FNLH_OK;
+  bool conv = false;
+  for (;;) {
+    if ((rc = residual_launch(m, J, sys, B, X, r, nullptr, nullptr, x_zero ? 1 : 0, norms, ws, s))) return rc;
+    x_zero = false;
+    FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
+    FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    bool finite = true;
+    for (int k = 0; k < K; ++k) {
+      const double rr = hn[2 * k], bb = hn[2 * k + 1];
+      if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) finite = false;
+      ck.rel[k] = (bb > 0.0) ? std::sqrt(rr / bb) : std::sqrt(rr);
+      worst = std::max(worst, ck.rel[k]);
+    }
+    if (!finite) {
+      rc = FNLH_ERR_NONFINITE;
+      break;
+    }
+    if (it == 0) ck.first_max = worst;
+    else if (worst > 1e3 * std::max(ck.first_max, 1e-300)) {
+      rc = FNLH_ERR_DIVERGED;
+      break;
+    }
+    conv = worst <= tol;
+    if (conv || it >= max_iterations) break;
+    if (masking) {
+      a.masked = 1;
+      for (int k = 0; k < K; ++k)
+        if (ck.rel[k] <= tol) a.active[k >> 6] &= ~(1ull << (k & 63));
+    }
+    for (int c = 0; c < ilu->n_colors; ++c) {
+      a.begin = ilu->color_ptr[c];
+      a.end = ilu->color_ptr[c + 1];
+      if (a.end <= a.begin) continue;
+      k_ilu_forward<BS, T><<<grid_for((long long)(a.end - a.begin) * K, kIluThreads), kIluThreads, 0, s>>>(a);
+      FNLH_LAUNCH_CHECK();
+    }
+    for (int c = ilu->n_colors - 1; c >= 0; --c) {
+      a.begin = ilu->color_ptr[c];
+      a.end = ilu->color_ptr[c + 1];
+      if (a.end <= a.begin) continue;
+      k_ilu_backward<BS, T><<<grid_for((long long)(a.end - a.begin) * K, kIluThreads), kIluThreads, 0, s>>>(a);
+      FNLH_LAUNCH_CHECK();
+    }
+    ++it;
+  }
+  if (iterations_done) *iterations_done = it;
+  if (rel_res)
+    for (int k = 0; k < K; ++k) rel_res[k] = ck.rel[k];
+  if (rc) return rc;
+  return conv ? FNLH_OK : FNLH_ERR_NOT_CONVERGED;
+}
+
+int solve_ilu_impl(const fnlh_mesh* m, const fnlh_jacobian* J, const fnlh_ilu* ilu, int n_harm, const double* omega,
+                   const double* sigma, const double* B, double* X, double tol, int max_iterations, int flags,
+                   void* ws, int* iterations_done, double* rel_res, cudaStream_t s) {
+  const Systems sys = make_systems(n_harm, omega, sigma);
+#define FNLH_ILU_SOLVE(BS, T) \
+  solve_ilu_typed<BS, T>(m, J, ilu, sys, B, X, tol, max_iterations, flags, ws, iterations_done, rel_res, s)
+  if (J->block == 5) return ilu->precision == FNLH_F64 ? FNLH_ILU_SOLVE(5, double) : FNLH_ILU_SOLVE(5, float);
+  return ilu->precision == FNLH_F64 ? FNLH_ILU_SOLVE(6, double) : FNLH_ILU_SOLVE(6, float);
+#undef FNLH_ILU_SOLVE
+}
+
+}  // namespace fnlh

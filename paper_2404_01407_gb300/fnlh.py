@@ -65,6 +65,11 @@ class fnlh_row(ctypes.Structure):
                 ("sigma", ctypes.POINTER(c_f64))]
 
 
+class fnlh_ilu(ctypes.Structure):
+    _fields_ = [("n_colors", c_i32), ("color", c_vp), ("order", c_vp), ("color_ptr", ctypes.POINTER(c_i32)),
+                ("factor", c_vp), ("factor_bytes", c_sz), ("precision", c_i32), ("n_harm", c_i32), ("ready", c_i32)]
+
+
 class fnlh_tuning(ctypes.Structure):
     _fields_ = [("threads", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32 * 2)]
 
@@ -102,6 +107,14 @@ _SIGS = {
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
     "fnlh_batched_extra_bytes": (c_sz, [c_i32]),
     "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
+    "fnlh_mesh_color": (ctypes.c_int, [c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, ctypes.POINTER(c_i32)]),
+    "fnlh_ilu_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
+    "fnlh_ilu_factor": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
+                                       ctypes.POINTER(c_f64), ctypes.POINTER(fnlh_ilu), c_vp, c_sz, c_vp]),
+    "fnlh_solve_ilu": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian),
+                                      ctypes.POINTER(fnlh_ilu), c_i32, ctypes.POINTER(c_f64), ctypes.POINTER(c_f64),
+                                      c_vp, c_vp, c_f64, c_i32, c_i32, c_vp, c_sz, ctypes.POINTER(c_i32),
+                                      ctypes.POINTER(c_f64), c_vp]),
     "fnlh_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
                                              ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp, c_vp, c_vp, c_vp,
                                              c_vp]),
@@ -384,3 +397,86 @@ def fnlh_residual_noalloc(dmesh, J, omega, B, X, r=None, norms=None, stream=None
                                      _ptr(r), _ptr(norms), _stream(stream))
     _check(st, "fnlh_residual_noalloc")
     return norms
+
+
+# ------------------------------------------------------------------ ILU(0)
+
+def fnlh_mesh_color(row_ptr, col_idx, max_colors=64):
+    """Greedy colouring (host): returns (color [n], order [n], color_ptr [n_colors + 1])."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    n = row_ptr.shape[0] - 1
+    color = np.zeros(max(n, 1), dtype=np.int32)
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    cptr = np.zeros(max_colors + 1, dtype=np.int32)
+    nc = c_i32(0)
+    col = col_idx if col_idx.size else np.zeros(1, dtype=np.int32)
+    st = lib().fnlh_mesh_color(n, row_ptr.ctypes.data_as(c_vp), col.ctypes.data_as(c_vp), int(max_colors),
+                               color.ctypes.data_as(c_vp), order.ctypes.data_as(c_vp), cptr.ctypes.data_as(c_vp),
+                               ctypes.byref(nc))
+    _check(st, "fnlh_mesh_color")
+    return color[:n].copy(), order[:n].copy(), cptr[: nc.value + 1].copy()
+
+
+def fnlh_ilu_bytes(n_nodes, block, n_harm, precision=FNLH_F64) -> int:
+    return int(lib().fnlh_ilu_bytes(n_nodes, block, n_harm, precision))
+
+
+class DeviceIlu:
+    """Colouring (device color/order, host color_ptr) and the factor buffer of
+    the ILU(0) smoother.  color: per-node colours (neighbours must differ); if
+    None the library's greedy colouring of the mesh is used."""
+
+    def __init__(self, dmesh: DeviceMesh, block: int, n_harm: int, color=None, precision=FNLH_F64, device="cuda"):
+        n = dmesh.n_nodes
+        if color is None:
+            color, order, cptr = fnlh_mesh_color(dmesh.row_ptr_host, dmesh.col_idx_host)
+        else:
+            color = np.ascontiguousarray(color, dtype=np.int32).reshape(n)
+            nc = int(color.max()) + 1 if n else 0
+            order = np.lexsort((np.arange(n), color)).astype(np.int32)
+            cptr = np.zeros(nc + 1, dtype=np.int32)
+            np.add.at(cptr, color + 1, 1)
+            cptr = np.cumsum(cptr).astype(np.int32)
+        dev = torch.device(device)
+        self.color_host, self.order_host = color, order
+        self.color_ptr = np.ascontiguousarray(cptr if len(cptr) else np.zeros(1, np.int32), dtype=np.int32)
+        self.color = torch.from_numpy(np.ascontiguousarray(color if n else np.zeros(1, np.int32))).to(dev)
+        self.order = torch.from_numpy(np.ascontiguousarray(order if n else np.zeros(1, np.int32))).to(dev)
+        nbytes = fnlh_ilu_bytes(n, block, n_harm, precision)
+        self.factor = torch.empty((max(nbytes, 16),), dtype=torch.uint8, device=dev)
+        self.c = fnlh_ilu(len(self.color_ptr) - 1, _ptr(self.color), _ptr(self.order),
+                          self.color_ptr.ctypes.data_as(ctypes.POINTER(c_i32)), _ptr(self.factor), nbytes,
+                          int(precision), 0, 0)
+
+    @property
+    def n_colors(self):
+        return int(self.c.n_colors)
+
+
+def fnlh_ilu_factor(dmesh, J, omega, ilu: DeviceIlu, ws=None, stream=None):
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    if ws is None:
+        ws = workspace(dmesh.n_nodes, J.block, n_harm, ilu.factor.device)
+    st = lib().fnlh_ilu_factor(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, ctypes.byref(ilu.c), _ptr(ws),
+                               ws.numel(), _stream(stream))
+    _check(st, "fnlh_ilu_factor")
+
+
+def fnlh_solve_ilu(dmesh, J, ilu: DeviceIlu, omega, B, X, tol, max_iterations, ws=None, stream=None, flags=0,
+                   sigma=None, raise_on_error=True):
+    """Returns (status, iterations_done, rel_res[K])."""
+    om, omp = _omega(omega)
+    n_harm = len(np.atleast_1d(omega))
+    sg, sgp = _sigma(sigma, n_harm)
+    if ws is None:
+        ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
+    its = c_i32(0)
+    rel = (c_f64 * (1 + n_harm))()
+    st = lib().fnlh_solve_ilu(ctypes.byref(dmesh.c), ctypes.byref(J.c), ctypes.byref(ilu.c), n_harm, omp, sgp,
+                              _ptr(B), _ptr(X), float(tol), int(max_iterations), int(flags), _ptr(ws), ws.numel(),
+                              ctypes.byref(its), rel, _stream(stream))
+    if raise_on_error and st != FNLH_OK:
+        raise FnlhError(st, "fnlh_solve_ilu")
+    return st, its.value, np.array(rel[:])

@@ -139,3 +139,81 @@ def test_tagged_mesh_validation_rejects_before_launch():
     n, nnz = 1000, 6000
     assert fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_TAGS) == \
         fnlh.fnlh_prep_bytes(n, nnz, 6, fnlh.FNLH_PREP_F64) + ((nnz * 4 + 255) // 256) * 256
+
+
+def _csr(mesh):
+    n, E = mesh.n_nodes, mesh.n_edges
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(max(2 * E, 1), np.int32)
+    ce = np.zeros(max(2 * E, 1), np.int32)
+    fnlh.fnlh_mesh_build_csr(n, E, mesh.edge_nodes, rp, ci, ce)
+    return rp, ci[: 2 * E]
+
+
+def _valid_coloring(rp, ci, color):
+    owner = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return np.all(color[owner] != color[ci])
+
+
+@pytest.mark.parametrize("dims,periodic,colors", [((7, 5, 3), False, 2), ((6, 4, 3), True, 2), ((6, 5, 3), True, 3)])
+def test_mesh_coloring_host_helper(dims, periodic, colors):
+    """Greedy colouring: a valid colouring, red-black on the lattice (and on an
+    even pitch), more colours where an odd pitch closes an odd cycle; the
+    order groups the nodes by colour."""
+    mesh = inputs.hex_mesh(*dims, periodic_y=periodic)
+    rp, ci = _csr(mesh)
+    color, order, cptr = fnlh.fnlh_mesh_color(rp, ci)
+    assert _valid_coloring(rp, ci, color)
+    if colors == 2:
+        assert len(cptr) - 1 == 2
+        assert np.array_equal(color, inputs.lattice_colors(dims))
+    else:
+        assert len(cptr) - 1 >= 3  # the odd cycle through the periodic edges
+    assert sorted(order) == list(range(mesh.n_nodes))
+    for c in range(len(cptr) - 1):
+        members = order[cptr[c]:cptr[c + 1]]
+        assert np.all(color[members] == c) and np.all(np.diff(members) > 0)
+
+
+def test_mesh_coloring_limits():
+    # a triangle needs three colours
+    rp = np.array([0, 2, 4, 6], np.int32)
+    ci = np.array([1, 2, 0, 2, 0, 1], np.int32)
+    color, order, cptr = fnlh.fnlh_mesh_color(rp, ci)
+    assert sorted(color) == [0, 1, 2]
+    with pytest.raises(fnlh.FnlhError):
+        fnlh.fnlh_mesh_color(rp, ci, max_colors=2)
+    with pytest.raises(fnlh.FnlhError):
+        fnlh.fnlh_mesh_color(rp, np.array([1, 2, 0, 7, 0, 1], np.int32))
+    # empty graph
+    c0, o0, p0 = fnlh.fnlh_mesh_color(np.zeros(1, np.int32), np.zeros(0, np.int32))
+    assert len(c0) == 0 and list(p0) == [0]
+
+
+def test_ilu_sizes_and_validation():
+    n = 1000
+    assert fnlh.fnlh_ilu_bytes(n, 6, 4) == n * 5 * 36 * 16
+    assert fnlh.fnlh_ilu_bytes(n, 6, 4, fnlh.FNLH_F32) == n * 5 * 36 * 8
+    assert fnlh.fnlh_ilu_bytes(n, 6, 4, fnlh.FNLH_BF16) == 0
+    assert fnlh.fnlh_ilu_bytes(n, 7, 4) == 0
+    L = fnlh.lib()
+    vol = ctypes.c_void_p(256)
+    m = fnlh.fnlh_mesh(4, 0, None, None, vol, vol, None, None, None, None)
+    J5 = fnlh.fnlh_jacobian(4, 0, 5, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, 0, 0, 0)
+    om = (ctypes.c_double * 1)(1.0)
+    cptr = (ctypes.c_int32 * 3)(0, 2, 4)
+    ilu = fnlh.fnlh_ilu(2, vol, vol, cptr, ctypes.c_void_p(4096), fnlh.fnlh_ilu_bytes(4, 5, 1), fnlh.FNLH_F64, 0, 0)
+    # not factored yet / wrong harmonic count
+    assert L.fnlh_solve_ilu(ctypes.byref(m), ctypes.byref(J5), ctypes.byref(ilu), 1, om, None, vol, vol, 1e-2, 10, 0,
+                            vol, 1 << 20, None, None, None) == fnlh.FNLH_ERR_WORKSPACE
+    # factor buffer too small, bad precision, colour offsets not covering the nodes
+    small = fnlh.fnlh_ilu(2, vol, vol, cptr, ctypes.c_void_p(4096), 16, fnlh.FNLH_F64, 0, 0)
+    assert L.fnlh_ilu_factor(ctypes.byref(m), ctypes.byref(J5), 1, om, ctypes.byref(small), vol, 1 << 20,
+                             None) == fnlh.FNLH_ERR_WORKSPACE
+    bad = fnlh.fnlh_ilu(2, vol, vol, cptr, ctypes.c_void_p(4096), 1 << 20, fnlh.FNLH_BF16, 0, 0)
+    assert L.fnlh_ilu_factor(ctypes.byref(m), ctypes.byref(J5), 1, om, ctypes.byref(bad), vol, 1 << 20,
+                             None) == fnlh.FNLH_ERR_ARG
+    short = (ctypes.c_int32 * 3)(0, 2, 3)
+    gap = fnlh.fnlh_ilu(2, vol, vol, short, ctypes.c_void_p(4096), 1 << 20, fnlh.FNLH_F64, 0, 0)
+    assert L.fnlh_ilu_factor(ctypes.byref(m), ctypes.byref(J5), 1, om, ctypes.byref(gap), vol, 1 << 20,
+                             None) == fnlh.FNLH_ERR_ARG
