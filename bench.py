@@ -478,6 +478,41 @@ def periodic_section(torch, fnlh, inputs, dev):
     return out
 
 
+def ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, reps=3):
+    """Colour passes of one ILU(0) iteration (forward + backward, all colours):
+    CUDA-event time on the launching stream (the library's timing hook brackets
+    the passes of the last iteration), algorithmic flops and bytes per
+    iteration, and their fractions of the FP64 peak and the measured HBM peak."""
+    n, b, N = p.mesh.n_nodes, p.block, p.n_harm
+    K, C = 1 + N, 1 + 2 * N
+    nnz = 2 * p.mesh.n_edges
+    color = ilu.color_host
+    rp, ci = dm.row_ptr_host, dm.col_idx_host
+    owner = np.repeat(np.arange(n), np.diff(rp))
+    n_upper = int(np.unique(owner[color[ci] > color[owner]]).shape[0])
+    flops = K * (4 * b * b * nnz + 8 * b * b * (n + n_upper))
+    if prec == fnlh.FNLH_F64:  # original basis: FP64 blocks, r read and x updated in the caller's layout
+        bytes_ = ((n + n_upper) * K * b * b * 2 * 8 + nnz * b * b * 8 + n * C * b * 8 + 4 * n * K * 2 * b * 8
+                  + 2 * n * C * b * 8 + nnz * 4 + n * 8)
+    else:  # Schur basis: FP32 blocks and rotated FP32 residual; x += Q e runs after the passes
+        bytes_ = ((n + n_upper) * K * b * b * 2 * 4 + nnz * b * b * 4 + n * K * 2 * b * 4 + 4 * n * K * 2 * b * 4
+                  + nnz * 4 + n * 8)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, z in ev:
+        a.record()
+        z.record()
+    for a, z in ev:
+        fnlh.fnlh_set_sweep_events(a, z)
+        fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, 0.0, 2, ws=ws, raise_on_error=False)
+    torch.cuda.synchronize()
+    fnlh.fnlh_set_sweep_events(None, None)
+    ms = sum(a.elapsed_time(z) for a, z in ev) / reps
+    peaks, _ = load_peaks()
+    return {"ms": ms, "flops": flops, "alg_bytes": bytes_, "tflops": flops / (ms * 1e-3) / 1e12,
+            "frac_fp64_peak": flops / (ms * 1e-3) / FP64_PEAK_FLOPS, "gbs": bytes_ / (ms * 1e-3) / 1e9,
+            "frac_hbm": bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
+
 def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
     """The paper's smoother, block ILU(0) in red-black order, against block
     Jacobi on the measured passage: iterations and time to a 1e-8 FP64
@@ -510,9 +545,29 @@ def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
                                                                  flags=zg, raise_on_error=False))
         out[name] = {"colors": ilu.n_colors, "factor_seconds": tf, "status": fnlh.fnlh_strerror(st),
                      "iterations": its, "seconds": t, "max_rel_residual": float(np.max(rel)),
-                     "stage_rule_iterations": its2, "factor_bytes": int(ilu.factor.numel())}
+                     "stage_rule_iterations": its2, "factor_bytes": int(ilu.factor.numel()),
+                     "passes": ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec)}
         del ilu
         torch.cuda.empty_cache()
+    # the colour passes read every array in colour order: with the nodes
+    # numbered by colour each pass streams contiguous memory
+    perm = np.argsort(inputs.lattice_colors(inputs.CONFIGS[WORKLOAD]["dims"]), kind="stable")
+    pm, _ = inputs.permute_mesh(p.mesh, perm=perm)
+    dmc = fnlh.DeviceMesh.from_mesh(pm, dev)
+    Jc = fnlh.DeviceJacobian(dmc, b, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32, dev)
+    fnlh.fnlh_build_jacobian(dmc, torch.from_numpy(p.q[perm]).to(dev), fnlh.make_params(p.cfl), Jc)
+    Bc = torch.from_numpy(p.b[perm]).to(dev)
+    for name, prec in (("ilu_f64_colour_numbered", fnlh.FNLH_F64), ("ilu_f32_colour_numbered", fnlh.FNLH_F32)):
+        ilu = fnlh.DeviceIlu(dmc, b, N, precision=prec, device=dev)
+        fnlh.fnlh_ilu_factor(dmc, Jc, p.omega, ilu, ws=ws)
+        t, (st, its, rel) = timed(lambda: fnlh.fnlh_solve_ilu(dmc, Jc, ilu, p.omega, Bc, X, tol, 200, ws=ws,
+                                                              flags=zg, raise_on_error=False))
+        out[name] = {"status": fnlh.fnlh_strerror(st), "iterations": its, "seconds": t,
+                     "max_rel_residual": float(np.max(rel)),
+                     "passes": ilu_pass_roofline(torch, fnlh, dmc, Jc, ilu, p, Bc, X, ws, prec)}
+        del ilu
+    del dmc, Jc, Bc
+    torch.cuda.empty_cache()
     for name, prec, inner in (("jacobi_f64", fnlh.FNLH_F64, 10), ("jacobi_f32", fnlh.FNLH_F32, 12)):
         t, (st, checks, sweeps, rel) = timed(lambda: fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200,
                                                                      ws=ws, flags=zg, raise_on_error=False))

@@ -320,9 +320,12 @@ typedef struct fnlh_ilu {
     const int32_t *color_ptr; /* HOST [n_colors + 1]: order[color_ptr[c] .. color_ptr[c+1]) have colour c */
     void *factor;             /* device, fnlh_ilu_bytes(n, b, n_harm, precision) bytes */
     size_t factor_bytes;
-    int32_t precision;        /* FNLH_F64: FP64 factor and iterations; FNLH_F32: FP32 factor and
-                                 correction passes (pivots formed in FP64 from the stored FP32
-                                 inverses of earlier colours), FP64 residual and update */
+    int32_t precision;        /* FNLH_F64: FP64 factor and passes on J's FP64 blocks.  FNLH_F32:
+                                 FP32 factor and passes in the per-node Schur basis of the sweeps
+                                 on the prep blob's FP32 blocks (needs FNLH_PREP_F32; the same
+                                 smoother, ILU(0) being invariant under that change of basis),
+                                 pivots formed in FP64 from the stored FP32 inverses of earlier
+                                 colours, FP64 residual and x += Q e with the sum in FP64 */
     int32_t n_harm;           /* systems the factor holds (set by fnlh_ilu_factor) */
     int32_t ready;            /* set to 1 by fnlh_ilu_factor */
 } fnlh_ilu;
@@ -356,8 +359,9 @@ int fnlh_solve_ilu(const fnlh_mesh *mesh, const fnlh_jacobian *J, const fnlh_ilu
 
 /* Timing hook (not part of the paper): when both are non-NULL, every later
  * relaxation on this host thread records `begin` on its stream right before
- * its first sweep launch and `end` right after its last one, so that the
- * caller can time the sweep launches alone.  Events are cudaEvent_t created
+ * its first sweep launch and `end` right after its last one (fnlh_solve_ilu:
+ * around the colour passes of each iteration, so the pair brackets the last
+ * one), so that the caller can time the sweep launches alone.  Events are cudaEvent_t created
  * by the caller; pass NULL, NULL to switch the hook off. */
 int fnlh_set_sweep_events(void *begin, void *end);
 

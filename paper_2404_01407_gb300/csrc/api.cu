@@ -344,6 +344,7 @@ int fnlh_ilu_factor(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_har
   FNLH_TRY(check_systems(n_harm, omega, nullptr));
   FNLH_TRY(check_tags(mesh, J));
   FNLH_TRY(check_ilu(mesh, J, ilu, n_harm));
+  if (ilu->precision == FNLH_F32) FNLH_TRY(check_prep(J, FNLH_F32));  // rotated FP32 blocks
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, FNLH_F64));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
   ilu->ready = 0;
@@ -365,6 +366,7 @@ int fnlh_solve_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_ilu
   FNLH_TRY(check_tags(mesh, J));
   FNLH_TRY(check_ilu(mesh, J, ilu, n_harm));
   if (!ilu->ready || ilu->n_harm != n_harm) return FNLH_ERR_WORKSPACE;
+  if (ilu->precision == FNLH_F32) FNLH_TRY(check_prep(J, FNLH_F32));
   if (!(tol >= 0.0) || max_iterations < 0) return FNLH_ERR_ARG;
   if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
   if (mesh->n_nodes > 0 && (!B || !X)) return FNLH_ERR_ARG;

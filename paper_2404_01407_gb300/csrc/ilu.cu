@@ -19,6 +19,15 @@
 //                                 x_i += y_i
 // with A_ij carrying the phase-lag factor of periodic entries.  An edge's two
 // couplings carry opposite phases, so the pivots do not depend on them.
+//
+// Precision: the FP64 smoother works in the original basis on J's FP64
+// blocks.  The FP32 smoother works in the per-node Schur basis of the sweeps
+// (x = Q x~), on the prep blob's FP32 rotated blocks: ILU(0) in pivot form is
+// invariant under that block-diagonal orthogonal change of basis (by
+// induction P~_i = Q_i^T P_i Q_i), so it is the same smoother, while every
+// block is read in FP32 without conversions; the FP64 residual is rotated to
+// FP32 on the fly and the correction is added back as x += Q e (product in
+// FP32, sum in FP64) -- the defect-correction pattern of the mixed sweeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,6 +46,9 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
                     const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
                     cudaStream_t s);
 Systems make_systems(int n_harm, const double* omega, const double* sigma);
+int mark_sweeps_begin(cudaStream_t s);
+int mark_sweeps_end(cudaStream_t s);
+int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s);
 
 // ------------------------------------------------------------- validation
 
@@ -96,11 +108,14 @@ struct IluArgs {
   const int32_t* color;
   const int32_t* row_ptr;
   const int32_t* cols;  // tagged column indices (col_of / side_of / cut_of)
-  const double* offd;   // J_ij, original basis
+  const double* offd;   // J_ij, original basis (FP64 smoother)
   const double* diag;
   const double* D;
   const double* vol;
-  void* factor;         // [n][K][b][b] complex inverse pivots (T)
+  const float* offd32;  // Q_i^T J_ij Q_j in FP32 (FP32 smoother)
+  const double* hess;   // Q_i^T (J_ii + D_i I) Q_i (FP32 smoother)
+  const float* r32;     // [n][K][b] complex Q^T r in FP32 (FP32 smoother)
+  void* factor;         // [n][b*b][K] complex inverse pivots (T), systems innermost
   const double* r;      // [n][C][b] residual, caller layout
   void* E;              // [n][K][b] complex work vector (T)
   double* X;            // [n][C][b] iterate, caller layout
@@ -121,6 +136,12 @@ __device__ __forceinline__ int find_in_row(const int32_t* row_ptr, const int32_t
   return -1;
 }
 
+// Factor entry e (row-major in the block) of node i, system k: the systems of
+// one entry are adjacent, so the K threads of a node read them coalesced.
+__host__ __device__ __forceinline__ size_t pivot_at(int i, int e, int k, int K, int BS) {
+  return (((size_t)i * BS * BS + e) * K + k) * 2;
+}
+
 // Pivot blocks of the nodes of one colour, thread per (node, system): P in
 // shared memory (complex, row-major), updated by every earlier-coloured
 // neighbour j with  P -= A_ij P_j^-1 A_ji  one row at a time, then inverted by
@@ -135,9 +156,10 @@ __global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_const
   const int i = a.order[t];
   double* P = sP[threadIdx.x];
   double* V = sV[threadIdx.x];
-  const double shift_re = a.D[i], shift_im = a.sys.omega[k] * a.vol[i];
+  constexpr bool kRot = sizeof(T) == 4;  // FP32 smoother: Schur basis, D inside hess
+  const double shift_re = kRot ? 0.0 : a.D[i], shift_im = a.sys.omega[k] * a.vol[i];
   for (int e = 0; e < BS * BS; ++e) {
-    P[2 * e] = a.diag[(size_t)i * BS * BS + e];
+    P[2 * e] = kRot ? a.hess[(size_t)i * BS * BS + e] : a.diag[(size_t)i * BS * BS + e];
     P[2 * e + 1] = 0.0;
   }
   for (int r = 0; r < BS; ++r) {
@@ -152,17 +174,18 @@ __global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_const
     if (a.color[j] >= ci) continue;
     const int q = find_in_row(a.row_ptr, a.cols, j, i);
     if (q < 0) continue;  // not reached on a symmetric pattern
-    const double* Aij = a.offd + (size_t)p * BS * BS;
-    const double* Aji = a.offd + (size_t)q * BS * BS;
-    const T* Pj = (const T*)a.factor + ((size_t)j * a.K + k) * 2 * BS * BS;
+    const size_t oij = (size_t)p * BS * BS, oji = (size_t)q * BS * BS;
+    const T* F = (const T*)a.factor;
     for (int r = 0; r < BS; ++r) {
       double wr[BS], wi[BS];  // row r of A_ij P_j^-1
       for (int cc = 0; cc < BS; ++cc) {
         double sr = 0.0, si = 0.0;
         for (int u = 0; u < BS; ++u) {
-          const double av = Aij[r * BS + u];
-          sr += av * (double)Pj[2 * (u * BS + cc)];
-          si += av * (double)Pj[2 * (u * BS + cc) + 1];
+          const size_t e = oij + r * BS + u;
+          const double av = kRot ? (double)a.offd32[e] : a.offd[e];
+          const size_t o = pivot_at(j, u * BS + cc, k, a.K, BS);
+          sr += av * (double)F[o];
+          si += av * (double)F[o + 1];
         }
         wr[cc] = sr;
         wi[cc] = si;
@@ -170,7 +193,8 @@ __global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_const
       for (int cc = 0; cc < BS; ++cc) {
         double sr = 0.0, si = 0.0;
         for (int u = 0; u < BS; ++u) {
-          const double av = Aji[u * BS + cc];
+          const size_t e = oji + u * BS + cc;
+          const double av = kRot ? (double)a.offd32[e] : a.offd[e];
           sr += wr[u] * av;
           si += wi[u] * av;
         }
@@ -235,16 +259,20 @@ __global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_const
     }
   }
   if (!ok) atomicOr(a.status, 2);
-  T* out = (T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS;
-  for (int e = 0; e < 2 * BS * BS; ++e) out[e] = ok ? (T)V[e] : T(0);
+  T* F = (T*)a.factor;
+  for (int e = 0; e < BS * BS; ++e) {
+    const size_t o = pivot_at(i, e, k, a.K, BS);
+    F[o] = ok ? (T)V[2 * e] : T(0);
+    F[o + 1] = ok ? (T)V[2 * e + 1] : T(0);
+  }
 }
 
 // --------------------------------------------------------------- apply
 
-// s -= A_ij e^{i side sigma} y_j for one neighbour slice (complex, T).
-template <int BS, typename T>
-__device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int k, T (&sr)[BS], T (&si)[BS],
-                                           T sign) {
+// s -= A_ij e^{i side sigma} y_j (kSubtract) or s += ... for one neighbour
+// slice (complex, T), accumulated straight into s.
+template <int BS, typename T, bool kSubtract>
+__device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int k, T (&sr)[BS], T (&si)[BS]) {
   const int j = col_of(cj);
   const T* yj = (const T*)a.E + ((size_t)j * a.K + k) * 2 * BS;
   T xr[BS], xi[BS];
@@ -254,33 +282,41 @@ __device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int 
     xi[t] = yj[2 * t + 1];
   }
   if (side_of(cj)) phase_shift<BS, T>(xr, xi, side_of(cj), a.sys.phase[k]);
-  const double* A = a.offd + (size_t)p * BS * BS;
 #pragma unroll
-  for (int r = 0; r < BS; ++r) {
-    T accr = 0, acci = 0;
+  for (int r = 0; r < BS; ++r)
 #pragma unroll
     for (int t = 0; t < BS; ++t) {
-      const T av = (T)__ldg(A + r * BS + t);
-      accr += av * xr[t];
-      acci += av * xi[t];
+      T av;
+      if constexpr (sizeof(T) == 4) av = __ldg(a.offd32 + (size_t)p * BS * BS + r * BS + t);
+      else av = __ldg(a.offd + (size_t)p * BS * BS + r * BS + t);
+      if constexpr (kSubtract) {
+        sr[r] -= av * xr[t];
+        si[r] -= av * xi[t];
+      } else {
+        sr[r] += av * xr[t];
+        si[r] += av * xi[t];
+      }
     }
-    sr[r] += sign * accr;
-    si[r] += sign * acci;
-  }
 }
 
-// (yr, yi) = P_i^-1 (sr, si), complex.
+template <typename T> struct Cplx2;
+template <> struct Cplx2<double> { using type = double2; };
+template <> struct Cplx2<float> { using type = float2; };
+
+// (yr, yi) = P_i^-1 (sr, si), complex; F points at the factor of node i,
+// system k (entry stride 2K values).
 template <int BS, typename T>
-__device__ __forceinline__ void ilu_pivot_apply(const T* __restrict__ Pinv, const T (&sr)[BS], const T (&si)[BS],
+__device__ __forceinline__ void ilu_pivot_apply(const T* __restrict__ F, int K, const T (&sr)[BS], const T (&si)[BS],
                                                 T (&yr)[BS], T (&yi)[BS]) {
+  using V2 = typename Cplx2<T>::type;
 #pragma unroll
   for (int r = 0; r < BS; ++r) {
     T ar = 0, ai = 0;
 #pragma unroll
     for (int t = 0; t < BS; ++t) {
-      const T pr = Pinv[2 * (r * BS + t)], pi = Pinv[2 * (r * BS + t) + 1];
-      ar += pr * sr[t] - pi * si[t];
-      ai += pr * si[t] + pi * sr[t];
+      const V2 p = __ldg(reinterpret_cast<const V2*>(F + (size_t)(r * BS + t) * 2 * K));
+      ar += p.x * sr[t] - p.y * si[t];
+      ai += p.x * si[t] + p.y * sr[t];
     }
     yr[r] = ar;
     yi[r] = ai;
@@ -293,25 +329,39 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_consta
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long t = a.begin + g / a.K;
   const int k = (int)(g % a.K);
-  if (t >= a.end || !ilu_active(a, k)) return;
+  if (t >= a.end) return;
   const int i = a.order[t];
-  const int C = a.sys.C;
-  const int c0 = (k == 0) ? 0 : 2 * k - 1;
-  T sr[BS], si[BS];
-  const double* rp = a.r + ((size_t)i * C + c0) * BS;
+  if (!ilu_active(a, k)) {  // a frozen system: no correction
+    T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
 #pragma unroll
-  for (int q = 0; q < BS; ++q) {
-    sr[q] = (T)rp[q];
-    si[q] = (k == 0) ? T(0) : (T)rp[BS + q];
+    for (int q = 0; q < 2 * BS; ++q) e[q] = T(0);
+    return;
+  }
+  T sr[BS], si[BS];
+  if constexpr (sizeof(T) == 4) {
+    const float* rp = a.r32 + ((size_t)i * a.K + k) * 2 * BS;
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      sr[q] = rp[2 * q];
+      si[q] = rp[2 * q + 1];
+    }
+  } else {
+    const int c0 = (k == 0) ? 0 : 2 * k - 1;
+    const double* rp = a.r + ((size_t)i * a.sys.C + c0) * BS;
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+      sr[q] = rp[q];
+      si[q] = (k == 0) ? 0.0 : rp[BS + q];
+    }
   }
   const int ci = a.color[i];
   for (int p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) {
     const int cj = a.cols[p];
     if (cut_of(cj) || a.color[col_of(cj)] >= ci) continue;
-    ilu_gather<BS, T>(a, p, cj, k, sr, si, T(-1));
+    ilu_gather<BS, T, true>(a, p, cj, k, sr, si);
   }
   T yr[BS], yi[BS];
-  ilu_pivot_apply<BS, T>((const T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS, sr, si, yr, yi);
+  ilu_pivot_apply<BS, T>((const T*)a.factor + pivot_at(i, 0, k, a.K, BS), a.K, sr, si, yr, yi);
   T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
@@ -340,7 +390,7 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_const
   for (int p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) {
     const int cj = a.cols[p];
     if (cut_of(cj) || a.color[col_of(cj)] <= ci) continue;
-    ilu_gather<BS, T>(a, p, cj, k, sr, si, T(1));
+    ilu_gather<BS, T, false>(a, p, cj, k, sr, si);
     any = true;
   }
   T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
@@ -352,7 +402,7 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_const
   }
   if (any) {
     T dr[BS], di[BS];
-    ilu_pivot_apply<BS, T>((const T*)a.factor + ((size_t)i * a.K + k) * 2 * BS * BS, sr, si, dr, di);
+    ilu_pivot_apply<BS, T>((const T*)a.factor + pivot_at(i, 0, k, a.K, BS), a.K, sr, si, dr, di);
 #pragma unroll
     for (int q = 0; q < BS; ++q) {
       yr[q] -= dr[q];
@@ -361,12 +411,13 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_const
       e[2 * q + 1] = yi[q];
     }
   }
-  const int C = a.sys.C;
-  double* xp = a.X + ((size_t)i * C + ((k == 0) ? 0 : 2 * k - 1)) * BS;
+  if constexpr (sizeof(T) == 8) {  // FP32: x += Q e after the passes
+    double* xp = a.X + ((size_t)i * a.sys.C + ((k == 0) ? 0 : 2 * k - 1)) * BS;
 #pragma unroll
-  for (int q = 0; q < BS; ++q) {
-    xp[q] += (double)yr[q];
-    if (k > 0) xp[BS + q] += (double)yi[q];
+    for (int q = 0; q < BS; ++q) {
+      xp[q] += yr[q];
+      if (k > 0) xp[BS + q] += yi[q];
+    }
   }
 }
 
@@ -377,6 +428,11 @@ static inline unsigned grid_for(long long count, int threads) { return (unsigned
 static IluArgs ilu_args(const fnlh_mesh* m, const fnlh_jacobian* J, const fnlh_ilu* ilu, const Systems& sys) {
   IluArgs a;
   std::memset(&a, 0, sizeof(a));
+  if (ilu->precision == FNLH_F32) {  // rotated FP32 blocks and the FP64 Schur factor
+    const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+    a.offd32 = at<float>(J->prep, L.offd32);
+    a.hess = at<double>(J->prep, L.hess);
+  }
   a.n = m->n_nodes;
   a.K = sys.K;
   a.order = ilu->order;
@@ -462,8 +518,15 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
   const WsLayout W = ws_layout(n, BS, K - 1, FNLH_F64);
   double* norms = at<double>(ws, W.norms);
   double* r = at<double>(ws, W.vec[0]);
+  constexpr bool kRot = sizeof(T) == 4;
+  const float* rotf = nullptr;
+  if (kRot) {
+    const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+    rotf = at<float>(J->prep, L.rotf);
+  }
   IluArgs a = ilu_args(m, J, ilu, sys);
   a.r = r;
+  a.r32 = (const float*)r;
   a.E = at<T>(ws, W.vec[1]);
   a.X = X;
   a.status = at<int32_t>(ws, W.status);
@@ -476,7 +539,10 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
   int it = 0, rc = FNLH_OK;
   bool conv = false;
   for (;;) {
-    if ((rc = residual_launch(m, J, sys, B, X, r, nullptr, nullptr, x_zero ? 1 : 0, norms, ws, s))) return rc;
+    // FP64: r in the caller's layout; FP32: Q^T r in FP32 straight from the residual kernel
+    if ((rc = residual_launch(m, J, sys, B, X, kRot ? nullptr : r, kRot ? (float*)r : nullptr, rotf, x_zero ? 1 : 0,
+                              norms, ws, s)))
+      return rc;
     x_zero = false;
     FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
     FNLH_CUDA_TRY(cudaStreamSynchronize(s));
@@ -504,6 +570,7 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
       for (int k = 0; k < K; ++k)
         if (ck.rel[k] <= tol) a.active[k >> 6] &= ~(1ull << (k & 63));
     }
+    if ((rc = mark_sweeps_begin(s))) return rc;
     for (int c = 0; c < ilu->n_colors; ++c) {
       a.begin = ilu->color_ptr[c];
       a.end = ilu->color_ptr[c + 1];
@@ -518,6 +585,8 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
       k_ilu_backward<BS, T><<<grid_for((long long)(a.end - a.begin) * K, kIluThreads), kIluThreads, 0, s>>>(a);
       FNLH_LAUNCH_CHECK();
     }
+    if ((rc = mark_sweeps_end(s))) return rc;
+    if (kRot && (rc = update_f32(n, K, BS, rotf, (const float*)a.E, X, s))) return rc;
     ++it;
   }
   if (iterations_done) *iterations_done = it;

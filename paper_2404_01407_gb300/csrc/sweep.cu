@@ -240,6 +240,20 @@ static inline int mark(cudaEvent_t ev, cudaStream_t s) {
   return FNLH_OK;
 }
 
+// x += Q e with the product in FP32 and the sum in FP64 (csrc/ilu.cu).
+int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s) {
+  const long long count = (long long)n * K;
+  if (count == 0) return FNLH_OK;
+  if (BS == 5) k_update_f32<5><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X);
+  else k_update_f32<6><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
+// The same hook for the ILU(0) passes (csrc/ilu.cu).
+int mark_sweeps_begin(cudaStream_t s) { return mark(g_ev_begin, s); }
+int mark_sweeps_end(cudaStream_t s) { return mark(g_ev_end, s); }
+
 constexpr size_t kMaxStageBytes = 200 * 1024;
 
 // Dynamic shared memory of a staged launch; tiles that need more than this

@@ -159,11 +159,14 @@ def custom_mesh(positions, edge_nodes, vol=None) -> Mesh:
                 normals=np.ascontiguousarray(normals), vol=np.asarray(vol, dtype=np.float64))
 
 
-def permute_mesh(mesh: Mesh, seed: int = 4) -> tuple[Mesh, np.ndarray]:
-    """Randomly renumber the nodes (locality stress variant). Returns (mesh, perm)
-    where new node ``p`` is old node ``perm[p]``."""
+def permute_mesh(mesh: Mesh, seed: int = 4, perm=None) -> tuple[Mesh, np.ndarray]:
+    """Renumber the nodes: randomly (locality stress variant) or by the given
+    permutation. Returns (mesh, perm) where new node ``p`` is old node
+    ``perm[p]``."""
     n = mesh.n_nodes
-    perm = np.random.default_rng(seed).permutation(n)
+    if perm is None:
+        perm = np.random.default_rng(seed).permutation(n)
+    perm = np.asarray(perm, dtype=np.int64)
     inv = np.empty(n, dtype=np.int64)
     inv[perm] = np.arange(n)
     en = inv[mesh.edge_nodes.astype(np.int64)]

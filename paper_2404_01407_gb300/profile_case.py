@@ -20,7 +20,7 @@ from . import fnlh, inputs
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["relax", "residual", "build", "solve"], default="relax")
+    ap.add_argument("--op", choices=["relax", "residual", "build", "solve", "ilu"], default="relax")
     ap.add_argument("--prec", choices=list(fnlh.PRECISIONS), default="f64")
     ap.add_argument("--dims", type=int, nargs=3, default=[128, 64, 48])
     ap.add_argument("--block", type=int, default=6)
@@ -34,13 +34,17 @@ def main():
     p = inputs.problem(tuple(a.dims), a.block, a.harm, a.cfl, name="profile")
     dev = torch.device("cuda")
     dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-    J = fnlh.DeviceJacobian(dm, a.block, fnlh.PREP_FOR[prec], dev)
+    J = fnlh.DeviceJacobian(dm, a.block, fnlh.PREP_FOR.get(prec, fnlh.FNLH_PREP_F64), dev)
     Q = torch.from_numpy(p.q).to(dev)
     params = fnlh.make_params(p.cfl)
     fnlh.fnlh_build_jacobian(dm, Q, params, J)
     B = torch.from_numpy(p.b).to(dev)
     X = torch.zeros_like(B)
     ws = fnlh.workspace(p.mesh.n_nodes, a.block, a.harm, dev)
+    ilu = None
+    if a.op == "ilu":  # factor once; each call runs `--sweeps` ILU(0) iterations
+        ilu = fnlh.DeviceIlu(dm, a.block, a.harm, precision=prec, device=dev)
+        fnlh.fnlh_ilu_factor(dm, J, p.omega, ilu, ws=ws)
 
     def op():
         if a.op == "relax":
@@ -49,6 +53,8 @@ def main():
             fnlh.fnlh_residual(dm, J, p.omega, B, X, ws=ws)
         elif a.op == "build":
             fnlh.fnlh_build_jacobian(dm, Q, params, J)
+        elif a.op == "ilu":
+            fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, 0.0, a.sweeps, ws=ws, raise_on_error=False)
         else:
             fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, a.sweeps, 50, ws=ws, flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
 
@@ -62,7 +68,7 @@ def main():
         e.record()
     e0.record()
     for r in range(a.reps):
-        if a.op == "relax":
+        if a.op in ("relax", "ilu"):
             fnlh.fnlh_set_sweep_events(*sw[r])
         op()
     e1.record()
@@ -73,6 +79,8 @@ def main():
            "finite": bool(np.isfinite(X.cpu().numpy()).all())}
     if a.op == "relax" and a.reps > 0 and a.sweeps > 0:
         out["ms_per_sweep"] = sum(b.elapsed_time(e) for b, e in sw) / (a.reps * a.sweeps)
+    if a.op == "ilu" and a.reps > 0 and a.sweeps > 0:  # the hook brackets the last iteration's passes
+        out["ms_passes_per_iteration"] = sum(b.elapsed_time(e) for b, e in sw) / a.reps
     print(json.dumps(out))
 
 

@@ -18,7 +18,7 @@ from tests import _gpu
 
 pytestmark = pytest.mark.gpu
 
-PREP = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_TAGS
+PREP = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_TAGS
 
 
 @pytest.fixture(scope="module", autouse=True)
