@@ -671,11 +671,11 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         c = inputs.CONFIGS[key]
         p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=key)
         dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-        J = fnlh.DeviceJacobian(dm, p.block, fnlh.PREP_FOR[prec], dev)
+        J = fnlh.DeviceJacobian(dm, p.block, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16, dev)
         fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
         B = torch.from_numpy(p.b).to(dev)
         rows.append((p, dm, J, B, torch.zeros_like(B),
-                     fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev, precision=prec)))
+                     fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev, precision=fnlh.FNLH_F64)))
     updates = sum(p.mesh.n_nodes * (1 + p.n_harm) for p, *_ in rows) * sweeps
 
     def per_row():
@@ -715,8 +715,42 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
             batched(best)
     torch.cuda.current_stream().wait_stream(s)
     t_graph = timeit(g.replay)
+    # the solve: mixed-precision batched defect correction against plain FP64 per-row solves, to 1e-8
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    solves = {}
+
+    def fp64_rows():
+        out = 0
+        for p, dm, J, B, X, ws in rows:
+            st, c, sw, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F64, 1e-8, 10, 200, ws=ws, flags=zg,
+                                             raise_on_error=False)
+            assert st == fnlh.FNLH_OK, fnlh.fnlh_strerror(st)
+            out = max(out, sw)
+        return out
+
+    for name, fn in (("fp64_per_row", fp64_rows),):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sw = fn()
+        torch.cuda.synchronize()
+        solves[name] = {"seconds": time.perf_counter() - t0, "max_sweeps": sw}
+    for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 12)):
+        sb = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
+        sws = torch.empty(sb.workspace_bytes(6, pc), dtype=torch.uint8, device=dev)
+        fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, c, sw, rel = fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        solves[f"batched_{pname}"] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": c, "sweeps": sw,
+                                      "max_rel_residual": float(np.max(rel)),
+                                      "speedup_vs_fp64_per_row": solves["fp64_per_row"]["seconds"] / t}
+        del sws
     return {"workload": "c4: rows 80x50x50 (N=2), 100x75x80 (N=8), 125x110x80 (N=4), b=6, "
                         f"{sweeps} {prec_name} sweeps", "per_row_ms": t_rows, "batched_ms": t_batch,
+            "solve_to_1e-8": solves,
             "batched_graph_ms": t_graph, "tuning": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm},
             "updates_per_s_graph": updates / (t_graph * 1e-3), "speedup_vs_per_row": t_rows / t_graph,
             "tuning_table": table}

@@ -268,6 +268,20 @@ int fnlh_relax_batched(const fnlh_row *rows, int32_t n_rows, int32_t sweeps, int
 
 size_t fnlh_batched_extra_bytes(int32_t n_rows);
 
+/* Batched fnlh_solve: every system of every row to ||r|| <= tol ||B||, all
+ * rows checked together.  FNLH_F64: plain Jacobi with the FP64 residual of
+ * every row every `inner_sweeps` sweeps (rows with `part` are rejected with
+ * FNLH_ERR_UNSUPPORTED: use a low precision).  FNLH_F32 / FNLH_BF16: defect
+ * correction -- FP64 residual of every row, then `inner_sweeps` batched
+ * launches over all rows from e = 0, then x += Q e per row.  flags, outputs
+ * and errors as fnlh_solve; rel_res (host, nullable) holds the rows' systems
+ * one row after the other.  workspace as fnlh_relax_batched, with each row's
+ * fnlh_workspace_bytes taken at `precision`.  SYNCHRONISING. */
+int fnlh_solve_batched(const fnlh_row *rows, int32_t n_rows, int32_t precision, double tol,
+                       int32_t inner_sweeps, int32_t max_checks, int32_t flags, const fnlh_tuning *tuning,
+                       void *workspace, size_t workspace_bytes, int32_t *checks_done, int32_t *sweeps_done,
+                       double *rel_res, fnlh_stream_t stream);
+
 /* Allocation-free variant of fnlh_residual (the paper has no counterpart).
  *
  * Same arguments, results and fixed-order sums as fnlh_residual, minus the

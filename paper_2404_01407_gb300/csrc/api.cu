@@ -20,6 +20,8 @@ int residual_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, cons
                     float*, const float*, int, double*, void*, cudaStream_t);
 Systems make_systems(int n_harm, const double* omega, const double* sigma);
 int batched_impl(const fnlh_row*, int, int, int, const fnlh_tuning*, void*, size_t, cudaStream_t);
+int solve_batched_impl(const fnlh_row*, int, int, double, int, int, int, const fnlh_tuning*, void*, int*, int*, double*,
+                       cudaStream_t);
 size_t batched_extra_bytes(int n_rows);
 void set_sweep_events(cudaEvent_t b, cudaEvent_t e);
 int residual_noalloc_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*,
@@ -275,6 +277,34 @@ int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int
   if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
   if (workspace_bytes < need) return FNLH_ERR_WORKSPACE;
   return batched_impl(rows, n_rows, sweeps, precision, tuning, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int fnlh_solve_batched(const fnlh_row* rows, int32_t n_rows, int32_t precision, double tol, int32_t inner_sweeps,
+                       int32_t max_checks, int32_t flags, const fnlh_tuning* tuning, void* workspace,
+                       size_t workspace_bytes, int32_t* checks_done, int32_t* sweeps_done, double* rel_res,
+                       fnlh_stream_t stream) {
+  if (!rows || n_rows < 1 || !valid_precision(precision)) return FNLH_ERR_ARG;
+  if (!(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
+  if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
+  size_t need = batched_extra_bytes(n_rows);
+  for (int r = 0; r < n_rows; ++r) {
+    const fnlh_row& R = rows[r];
+    FNLH_TRY(check_mesh(R.mesh, false));
+    FNLH_TRY(check_jac(R.mesh, R.J));
+    FNLH_TRY(check_systems(R.n_harm, R.omega, R.sigma));
+    FNLH_TRY(check_prep(R.J, precision));
+    FNLH_TRY(check_tags(R.mesh, R.J));
+    // plain FP64 Jacobi on the truncated sweeps would not reach the full system's solution
+    if (precision == FNLH_F64 && R.mesh->part) return FNLH_ERR_UNSUPPORTED;
+    if (R.mesh->n_nodes > 0 && (!R.B || !R.X)) return FNLH_ERR_ARG;
+    FNLH_TRY(check_pairs(R.mesh->n_nodes, R.n_harm));
+    need += ws_layout(R.mesh->n_nodes, R.J->block, R.n_harm, precision).total;
+  }
+  if (!workspace) return FNLH_ERR_WORKSPACE;
+  if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
+  if (workspace_bytes < need) return FNLH_ERR_WORKSPACE;
+  return solve_batched_impl(rows, n_rows, precision, tol, inner_sweeps, max_checks, flags, tuning, workspace,
+                            checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
 }
 
 int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,

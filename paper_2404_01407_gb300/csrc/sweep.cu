@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "sweep_kernel.cuh"
@@ -514,12 +515,15 @@ struct BatchRow {
   TileRow row;
   void* x[2];        // ping-pong iterate buffers
   long long tile0;   // first global tile of this row
+  int32_t masked;    // 0: every system is swept; 1: only the systems set in `active`
+  int32_t pad;
+  uint64_t active[2];
   double omega[kMaxSys];
   double2 phase[kMaxSys];
 };
 
 struct BatchArgs {
-  int32_t n_rows, parity, smem_floats, pad;
+  int32_t n_rows, parity, smem_floats, x_zero;  // x_zero: the iterate is zero (first sweep of a correction)
   long long n_tiles;
   BatchRow row[kMaxBatchRows];
 };
@@ -530,13 +534,18 @@ __device__ __forceinline__ void batched_tile(const BatchArgs& a, long long t, fl
   int r = 0;
   while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
   const BatchRow& D = a.row[r];
-  const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, nullptr, D.phase};
+  const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, D.masked ? D.active : nullptr, D.phase};
   const long long g0 = (t - D.tile0) * blockDim.x;
   if constexpr (sizeof(T) == 8) {
     const long long g = g0 + threadIdx.x;
-    if (g < (long long)D.row.n * D.row.K) sweep_pair_f64<BS>(D.row, io, g, false);
+    if (g < (long long)D.row.n * D.row.K) {
+      const int i = (int)fdiv((uint32_t)g, D.row.divK);
+      const int k = (int)g - i * D.row.K;
+      if (sys_active(io, k)) sweep_pair_f64<BS>(D.row, io, g, a.x_zero != 0);
+      else freeze_pair<BS, double>(D.row, io, i, k, a.x_zero != 0);
+    }
   } else {
-    sweep_tile_f32<BS, TJ>(D.row, io, g0, false, smem, a.smem_floats);
+    sweep_tile_f32<BS, TJ>(D.row, io, g0, a.x_zero != 0, smem, a.smem_floats);
   }
 }
 
@@ -560,14 +569,24 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched_persistent(c
 
 size_t batched_extra_bytes(int n_rows) { return n_rows > 0 ? 256 : 0; }
 
+// Launch shape, operands and workspace slices of a batch.
+struct BatchPlan {
+  int threads;
+  unsigned grid;
+  bool persistent;
+  size_t smem;
+  SweepOperands ops[kMaxBatchRows];
+  Systems sys[kMaxBatchRows];
+  char* base[kMaxBatchRows];  // the row's workspace slice (ws_layout of its size and precision)
+};
+
 template <int BS, typename TJ, typename T>
-int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, const fnlh_tuning* tn, void* ws,
-                  cudaStream_t s) {
-  static thread_local BatchArgs a;  // large: kept off the stack (the launch copies it)
+int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuning* tn, void* ws, BatchArgs& a,
+                BatchPlan& P) {
   std::memset(&a, 0, sizeof(a));
-  const int threads = (tn && tn->threads > 0) ? tn->threads : (sizeof(T) == 4 ? kSweepThreadsF32 : kSweepThreads);
+  P.threads = (tn && tn->threads > 0) ? tn->threads : (sizeof(T) == 4 ? kSweepThreadsF32 : kSweepThreads);
   const int ctas_per_sm = tn ? tn->ctas_per_sm : 0;  // 0: one CTA per tile
-  if (threads > kSweepThreads || threads % 32) return FNLH_ERR_ARG;
+  if (P.threads > kSweepThreads || P.threads % 32) return FNLH_ERR_ARG;
   int dev = 0, sms = 0;
   FNLH_CUDA_TRY(cudaGetDevice(&dev));
   FNLH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -575,14 +594,15 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   long long tiles = 0;
   int kmin = kMaxSys;
   a.n_rows = n_rows;
-  SweepOperands ops[kMaxBatchRows];
   for (int r = 0; r < n_rows; ++r) {
     const fnlh_row& R = rows[r];
-    int rc = sweep_operands(R.mesh, R.J, precision, &ops[r]);
+    int rc = sweep_operands(R.mesh, R.J, precision, &P.ops[r]);
     if (rc) return rc;
-    const Systems sys = make_systems(R.n_harm, R.omega, R.sigma);
+    P.sys[r] = make_systems(R.n_harm, R.omega, R.sigma);
+    const Systems& sys = P.sys[r];
     const WsLayout W = ws_layout(R.mesh->n_nodes, BS, R.n_harm, precision);
     char* base = (char*)ws + off;
+    P.base[r] = base;
     off += W.total;
     BatchRow& D = a.row[r];
     D.row.n = R.mesh->n_nodes;
@@ -590,61 +610,209 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
     D.row.divK = make_fastdiv((uint32_t)sys.K);
     D.row.stage = sys.K >= kStageMinSystems ? 1 : 0;
     D.row.row_ptr = R.mesh->row_ptr;
-    D.row.col_idx = ops[r].cols;
-    D.row.offd = ops[r].offd;
-    D.row.hess = ops[r].hess;
+    D.row.col_idx = P.ops[r].cols;
+    D.row.offd = P.ops[r].offd;
+    D.row.hess = P.ops[r].hess;
     D.row.vol = R.mesh->vol;
     D.row.Bt = base + W.vec[0];
     D.x[0] = base + W.vec[1];
     D.x[1] = base + W.vec[2];
     D.tile0 = tiles;
-    tiles += ((long long)D.row.n * D.row.K + threads - 1) / threads;
+    D.active[0] = D.active[1] = ~0ull;
+    tiles += ((long long)D.row.n * D.row.K + P.threads - 1) / P.threads;
     if (D.row.stage) kmin = std::min(kmin, sys.K);
     for (int k = 0; k < kMaxSys; ++k) {
       D.omega[k] = sys.omega[k];
       D.phase[k] = sys.phase[k];
     }
-    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.B, (T*)D.row.Bt, s))) return rc;
-    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, ops[r].rot, R.X, (T*)D.x[0], s))) return rc;
   }
   a.n_tiles = tiles;
-  size_t smem = 0;
-  const bool persistent = ctas_per_sm > 0;
+  P.smem = 0;
+  P.persistent = ctas_per_sm > 0;
   if constexpr (sizeof(T) == 4) {
     // sized for the staged row with the fewest systems (the largest stage),
     // so that every staged row's tiles fit
     if (kmin < kMaxSys) {
-      int rc = persistent
-                   ? stage_setup(k_sweep_batched_persistent<BS, TJ, T>, threads, kmin, BS, &a.smem_floats, &smem)
-                   : stage_setup(k_sweep_batched<BS, TJ, T>, threads, kmin, BS, &a.smem_floats, &smem);
+      int rc = P.persistent ? stage_setup(k_sweep_batched_persistent<BS, TJ, T>, P.threads, kmin, BS,
+                                          &a.smem_floats, &P.smem)
+                            : stage_setup(k_sweep_batched<BS, TJ, T>, P.threads, kmin, BS, &a.smem_floats, &P.smem);
       if (rc) return rc;
     }
   }
-  const long long grid_ll = persistent ? std::min<long long>(tiles, (long long)sms * ctas_per_sm) : tiles;
-  const unsigned grid = (unsigned)std::max<long long>(grid_ll, 1);
-  {
-    int rc = mark(g_ev_begin, s);
-    if (rc) return rc;
-  }
+  const long long grid_ll = P.persistent ? std::min<long long>(tiles, (long long)sms * ctas_per_sm) : tiles;
+  P.grid = (unsigned)std::max<long long>(grid_ll, 1);
+  return FNLH_OK;
+}
+
+// `sweeps` launches starting at a.parity (the first from zero when x_zero);
+// a.parity holds the buffer of the result on return.
+template <int BS, typename TJ, typename T>
+int batch_launch(BatchArgs& a, const BatchPlan& P, int sweeps, int x_zero, cudaStream_t s) {
+  int rc = mark(g_ev_begin, s);
+  if (rc) return rc;
   for (int it = 0; it < sweeps; ++it) {
-    a.parity = it & 1;
-    if (tiles > 0) {
-      if (persistent) k_sweep_batched_persistent<BS, TJ, T><<<grid, threads, smem, s>>>(a);
-      else k_sweep_batched<BS, TJ, T><<<grid, threads, smem, s>>>(a);
+    a.x_zero = (it == 0) ? x_zero : 0;
+    if (a.n_tiles > 0) {
+      if (P.persistent) k_sweep_batched_persistent<BS, TJ, T><<<P.grid, P.threads, P.smem, s>>>(a);
+      else k_sweep_batched<BS, TJ, T><<<P.grid, P.threads, P.smem, s>>>(a);
       FNLH_LAUNCH_CHECK();
     }
+    a.parity ^= 1;
   }
-  {
-    int rc = mark(g_ev_end, s);
-    if (rc) return rc;
-  }
-  const int fin = sweeps & 1;
+  a.x_zero = 0;
+  return mark(g_ev_end, s);
+}
+
+static thread_local BatchArgs g_batch;  // large: kept off the stack (each launch copies it)
+
+template <int BS, typename TJ, typename T>
+int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, const fnlh_tuning* tn, void* ws,
+                  cudaStream_t s) {
+  BatchArgs& a = g_batch;
+  BatchPlan P;
+  int rc = batch_setup<BS, TJ, T>(rows, n_rows, precision, tn, ws, a, P);
+  if (rc) return rc;
   for (int r = 0; r < n_rows; ++r) {
     const BatchRow& D = a.row[r];
-    int rc = rotate_out<BS, T>(D.row.n, D.row.K, ops[r].rot, (const T*)D.x[fin], rows[r].X, 0, s);
-    if (rc) return rc;
+    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].B, (T*)D.row.Bt, s))) return rc;
+    if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].X, (T*)D.x[0], s))) return rc;
+  }
+  a.parity = 0;
+  if ((rc = batch_launch<BS, TJ, T>(a, P, sweeps, 0, s))) return rc;
+  for (int r = 0; r < n_rows; ++r) {
+    const BatchRow& D = a.row[r];
+    if ((rc = rotate_out<BS, T>(D.row.n, D.row.K, P.ops[r].rot, (const T*)D.x[a.parity], rows[r].X, 0, s))) return rc;
   }
   return FNLH_OK;
+}
+
+// Batched solve: every row's systems to ||r|| <= tol ||B|| together.  FP64:
+// plain Jacobi in the rotated basis with the FP64 residual every `inner`
+// sweeps; FP32 / BF16: defect correction (FP64 residual of every row, one
+// batched launch per inner sweep from e = 0 over all rows, x += Q e).
+template <int BS, typename TJ, typename T>
+int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double tol, int inner, int max_checks,
+                        int flags, const fnlh_tuning* tn, void* ws, int* checks_done, int* sweeps_done,
+                        double* rel_res, cudaStream_t s) {
+  BatchArgs& a = g_batch;
+  BatchPlan P;
+  int rc = batch_setup<BS, TJ, T>(rows, n_rows, precision, tn, ws, a, P);
+  if (rc) return rc;
+  const bool mixed = sizeof(T) == 4;
+  const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
+  bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
+  int32_t* status = at<int32_t>(P.base[0], 0);
+  for (int r = 0; r < n_rows; ++r) {
+    const BatchRow& D = a.row[r];
+    if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(rows[r].X, 0, sizeof(double) * (size_t)D.row.n * P.sys[r].C * BS, s));
+    if (!mixed) {
+      if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].B, (T*)D.row.Bt, s))) return rc;
+      if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].X, (T*)D.x[0], s))) return rc;
+    }
+  }
+  FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+  a.parity = 0;
+  std::vector<double> hn(2 * kMaxSys * n_rows);
+  std::vector<double> rel(kMaxSys * n_rows, 0.0);
+  double first_max = 0.0;
+  int checks = 0, sweeps = 0;
+  bool conv = false;
+  for (;;) {
+    for (int r = 0; r < n_rows; ++r) {
+      const BatchRow& D = a.row[r];
+      const WsLayout W = ws_layout(D.row.n, BS, D.row.K - 1, precision);
+      double* norms = at<double>(P.base[r], W.norms);
+      rc = residual_launch(rows[r].mesh, rows[r].J, P.sys[r], rows[r].B, rows[r].X, nullptr,
+                           mixed ? (float*)D.row.Bt : nullptr, P.ops[r].rotf, x_zero ? 1 : 0, norms, P.base[r], s);
+      if (rc) return rc;
+      FNLH_CUDA_TRY(cudaMemcpyAsync(hn.data() + 2 * kMaxSys * r, norms, sizeof(double) * 2 * D.row.K,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    x_zero = false;
+    int32_t hstatus = 0;
+    FNLH_CUDA_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hstatus) {
+      rc = FNLH_ERR_TIMEOUT;
+      break;
+    }
+    double worst = 0.0;
+    bool finite = true;
+    for (int r = 0; r < n_rows; ++r)
+      for (int k = 0; k < a.row[r].row.K; ++k) {
+        const double rr = hn[2 * kMaxSys * r + 2 * k], bb = hn[2 * kMaxSys * r + 2 * k + 1];
+        if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) finite = false;
+        const double v = (bb > 0.0) ? std::sqrt(rr / bb) : std::sqrt(rr);
+        rel[kMaxSys * r + k] = v;
+        worst = std::max(worst, v);
+      }
+    if (!finite) {
+      rc = FNLH_ERR_NONFINITE;
+      break;
+    }
+    if (checks == 0) first_max = worst;
+    else if (worst > 1e3 * std::max(first_max, 1e-300)) {
+      rc = FNLH_ERR_DIVERGED;
+      break;
+    }
+    ++checks;
+    conv = worst <= tol;
+    if (conv || checks >= max_checks) break;
+    if (masking)  // converged systems are frozen for the following sweeps
+      for (int r = 0; r < n_rows; ++r) {
+        BatchRow& D = a.row[r];
+        D.masked = 1;
+        for (int k = 0; k < D.row.K; ++k)
+          if (rel[kMaxSys * r + k] <= tol) D.active[k >> 6] &= ~(1ull << (k & 63));
+      }
+    if (mixed) {
+      a.parity = 0;
+      if ((rc = batch_launch<BS, TJ, T>(a, P, inner, 1, s))) return rc;
+      for (int r = 0; r < n_rows; ++r) {
+        const BatchRow& D = a.row[r];
+        if ((rc = update_f32(D.row.n, D.row.K, BS, P.ops[r].rotf, (const float*)D.x[a.parity], rows[r].X, s)))
+          return rc;
+      }
+    } else {
+      if ((rc = batch_launch<BS, TJ, T>(a, P, inner, 0, s))) return rc;
+      for (int r = 0; r < n_rows; ++r) {
+        const BatchRow& D = a.row[r];
+        if ((rc = rotate_out<BS, T>(D.row.n, D.row.K, P.ops[r].rot, (const T*)D.x[a.parity], rows[r].X, 0, s)))
+          return rc;
+      }
+    }
+    sweeps += inner;
+  }
+  if (checks_done) *checks_done = checks;
+  if (sweeps_done) *sweeps_done = sweeps;
+  if (rel_res) {
+    int o = 0;
+    for (int r = 0; r < n_rows; ++r)
+      for (int k = 0; k < a.row[r].row.K; ++k) rel_res[o++] = rel[kMaxSys * r + k];
+  }
+  if (rc) return rc;
+  return conv ? FNLH_OK : FNLH_ERR_NOT_CONVERGED;
+}
+
+int solve_batched_impl(const fnlh_row* rows, int n_rows, int precision, double tol, int inner, int max_checks,
+                       int flags, const fnlh_tuning* tn, void* ws, int* checks_done, int* sweeps_done, double* rel_res,
+                       cudaStream_t s) {
+  if (n_rows > kMaxBatchRows) return FNLH_ERR_UNSUPPORTED;
+  const int b = rows[0].J->block;
+  for (int r = 1; r < n_rows; ++r)
+    if (rows[r].J->block != b) return FNLH_ERR_UNSUPPORTED;
+#define FNLH_SB(BS, TJ, T) \
+  solve_batched_typed<BS, TJ, T>(rows, n_rows, precision, tol, inner, max_checks, flags, tn, ws, checks_done, \
+                                 sweeps_done, rel_res, s)
+  if (b == 5) {
+    if (precision == FNLH_F64) return FNLH_SB(5, double, double);
+    if (precision == FNLH_F32) return FNLH_SB(5, float, float);
+    return FNLH_SB(5, __nv_bfloat16, float);
+  }
+  if (precision == FNLH_F64) return FNLH_SB(6, double, double);
+  if (precision == FNLH_F32) return FNLH_SB(6, float, float);
+  return FNLH_SB(6, __nv_bfloat16, float);
+#undef FNLH_SB
 }
 
 int batched_impl(const fnlh_row* rows, int n_rows, int sweeps, int precision, const fnlh_tuning* tn, void* ws,

@@ -106,6 +106,9 @@ _SIGS = {
     "fnlh_relax_batched": (ctypes.c_int, [ctypes.POINTER(fnlh_row), c_i32, c_i32, c_i32,
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, c_vp]),
     "fnlh_batched_extra_bytes": (c_sz, [c_i32]),
+    "fnlh_solve_batched": (ctypes.c_int, [ctypes.POINTER(fnlh_row), c_i32, c_i32, c_f64, c_i32, c_i32, c_i32,
+                                          ctypes.POINTER(fnlh_tuning), c_vp, c_sz, ctypes.POINTER(c_i32),
+                                          ctypes.POINTER(c_i32), ctypes.POINTER(c_f64), c_vp]),
     "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
     "fnlh_mesh_color": (ctypes.c_int, [c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, ctypes.POINTER(c_i32)]),
     "fnlh_ilu_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
@@ -362,10 +365,10 @@ class BatchedRows:
         self.arr = arr
         self.n = len(rows)
 
-    def workspace_bytes(self, block):
+    def workspace_bytes(self, block, precision=FNLH_F64):
         total = int(lib().fnlh_batched_extra_bytes(self.n))
         for dm, J, om, B, X in self.keep:
-            total += fnlh_workspace_bytes(dm.n_nodes, block, (B.shape[1] - 1) // 2)
+            total += fnlh_workspace_bytes(dm.n_nodes, block, (B.shape[1] - 1) // 2, precision)
         return total
 
 
@@ -374,6 +377,21 @@ def fnlh_relax_batched(batch: BatchedRows, sweeps, precision, tuning=None, ws=No
     st = lib().fnlh_relax_batched(batch.arr, batch.n, int(sweeps), int(precision), tn, _ptr(ws), ws.numel(),
                                   _stream(stream))
     _check(st, "fnlh_relax_batched")
+
+
+def fnlh_solve_batched(batch: BatchedRows, precision, tol, inner_sweeps, max_checks, tuning=None, ws=None,
+                       stream=None, flags=0, raise_on_error=True):
+    """Returns (status, checks_done, sweeps_done, rel_res[sum of K over rows])."""
+    tn = ctypes.byref(tuning) if tuning is not None else None
+    checks, sweeps = c_i32(0), c_i32(0)
+    total = sum((B.shape[1] - 1) // 2 + 1 for (_, _, _, B, _) in batch.keep)
+    rel = (c_f64 * total)()
+    st = lib().fnlh_solve_batched(batch.arr, batch.n, int(precision), float(tol), int(inner_sweeps), int(max_checks),
+                                  int(flags), tn, _ptr(ws), ws.numel(), ctypes.byref(checks), ctypes.byref(sweeps),
+                                  rel, _stream(stream))
+    if raise_on_error and st != FNLH_OK:
+        raise FnlhError(st, "fnlh_solve_batched")
+    return st, checks.value, sweeps.value, np.array(rel[:])
 
 
 def fnlh_set_sweep_events(begin=None, end=None):

@@ -1,0 +1,103 @@
+"""GPU: batched solve over several blade rows (one launch per inner sweep
+covering every row) against the per-row solves and the oracle.
+
+With tol = 0 both run the same number of checks and sweeps: the mixed
+batched solve equals the per-row mixed solves bit for bit (same tile body,
+residual and update), the FP64 batched solve equals the per-row FP64 solves
+to 1e-13 (the batched FP64 tile takes the complex path for the mean flow).
+Solved to 1e-8, every row's true FP64 residual (oracle) is below 1e-8.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_01407_gb300 import fnlh, inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available()
+    fnlh.lib()
+
+
+def rows_problem():
+    return [inputs.problem((9, 7, 5), 6, 2, 20.0, 1.0, seeds=(1, 2, 3)),
+            inputs.problem((12, 8, 6), 6, 8, 20.0, 1.6, seeds=(4, 5, 6)),
+            inputs.problem((10, 9, 7), 6, 4, 20.0, 2.3, seeds=(7, 8, 9))]
+
+
+def device_rows(probs, part=None):
+    dev = []
+    for q, p in enumerate(probs):
+        pa = None if part is None else part[q]
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, "cuda", part=pa)
+        J = fnlh.DeviceJacobian(dm, p.block, _gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).cuda(), fnlh.make_params(p.cfl), J)
+        dev.append((p, dm, J, torch.from_numpy(p.b).cuda()))
+    return dev
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16, fnlh.FNLH_F64])
+def test_batched_solve_equals_per_row_solves(prec):
+    dev = device_rows(rows_problem())
+    inner, checks = 6, 4
+    singles = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        st, c, sw, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 0.0, inner, checks, raise_on_error=False)
+        assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks
+        singles.append(X.cpu().numpy())
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 0.0, inner, checks, ws=ws, raise_on_error=False)
+    assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks and sw == inner * (checks - 1)
+    assert rel.shape == (3 + 9 + 5,)
+    for X, ref, (p, *_r) in zip(Xs, singles, dev):
+        if prec == fnlh.FNLH_F64:
+            err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+            assert np.all(err <= 1e-13), err
+        else:
+            assert np.array_equal(X.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_batched_mixed_solve_reaches_1e8(prec):
+    probs = rows_problem()
+    dev = device_rows(probs)
+    Xs = [torch.full_like(B, 7.0) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+    flags = fnlh.FNLH_SOLVE_ZERO_GUESS | fnlh.FNLH_SOLVE_MASK_CONVERGED
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 1e-8, 12, 60, ws=ws, flags=flags)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    for X, p in zip(Xs, probs):
+        oj = _gpu.oracle_jacobian(p)
+        true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+        assert np.all(true_rel <= 1.05e-8), true_rel
+
+
+def test_batched_solve_with_partitioned_and_periodic_rows():
+    probs = [inputs.problem((12, 8, 6), 6, 4, 20.0, 1.6, seeds=(4, 5, 6)),
+             inputs.problem((10, 6, 7), 6, 3, 20.0, 2.3, seeds=(7, 8, 9), periodic=True)]
+    parts = [inputs.box_partition((12, 8, 6), (2, 2, 1)), None]
+    dev = device_rows(probs, parts)
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X, p.phase) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32), dtype=torch.uint8, device="cuda")
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F32, 1e-8, 12, 60, ws=ws)
+    assert st == fnlh.FNLH_OK
+    for X, p in zip(Xs, probs):
+        m = p.mesh
+        oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl, periodic=m.periodic)
+        true_rel = oracle.rel_residuals(oj, m.vol, p.omega, p.b, X.cpu().numpy(), sigma=p.phase)
+        assert np.all(true_rel <= 1.05e-8), true_rel
+    ws64 = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
+    with pytest.raises(fnlh.FnlhError) as e:
+        fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F64, 1e-8, 10, 60, ws=ws64)
+    assert e.value.status == fnlh.FNLH_ERR_UNSUPPORTED
