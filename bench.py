@@ -332,7 +332,8 @@ def run_fnlh(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hex passage; see DESIGN.md)",
             "config": workload_config(p), "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
-            "final_rel_residual": [float(x) for x in rel], "peaks_source": peaks_kind}
+            "final_rel_residual": [float(x) for x in rel],
+            "final_rel_residual_Rz": float(np.sqrt(np.mean(np.square(rel)))), "peaks_source": peaks_kind}
 
     if rank == 0 and world == 1 and not args.no_extras:
         del J, ws

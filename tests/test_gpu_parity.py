@@ -367,3 +367,51 @@ def test_batched_rows_other_precisions(prec):
             assert np.all(err <= 1e-13), err
         else:
             assert np.array_equal(X.cpu().numpy(), ref)
+
+
+def test_literal_reading_shift_by_D():
+    """The literal reading of the spectral term, i omega D instead of i omega V:
+    the per-node scalar of the shift is the mesh's `vol` array, so passing D
+    there gives it; the Jacobian build does not read `vol`."""
+    p = small("b6n4")
+    oj = _gpu.oracle_jacobian(p)
+    mesh_d = inputs.Mesh(p.mesh.dims, p.mesh.positions, p.mesh.edge_nodes, p.mesh.normals, oj.D.copy())
+    pd = inputs.Problem(mesh_d, p.q, p.b, p.omega, p.block, p.cfl)
+    dm, J, B = _gpu.device_problem(pd)
+    assert np.allclose(J.D.cpu().numpy(), oj.D, rtol=1e-14, atol=0)  # same build with vol replaced
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 30, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, oj.D, p.omega, p.b, 30)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+    # and the max-norm view of the same comparison
+    x = X.cpu().numpy()
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_relax_and_residual_capture_in_a_cuda_graph():
+    """fnlh_relax and fnlh_residual are asynchronous and allocate nothing: a
+    captured graph replays them with the same result as direct calls."""
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda")
+    X_direct = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X_direct, 12, fnlh.FNLH_F32, ws)
+    n_direct = fnlh.fnlh_residual(dm, J, p.omega, B, X_direct, ws=ws).clone()
+    X = torch.zeros_like(B)
+    norms = torch.empty((1 + p.n_harm, 2), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside the capture (kernel attributes, lazy loading)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, 12, fnlh.FNLH_F32, ws, stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fnlh.fnlh_relax(dm, J, p.omega, B, X, 12, fnlh.FNLH_F32, ws, stream=s)
+            fnlh.fnlh_residual(dm, J, p.omega, B, X, norms=norms, ws=ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    X.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(X, X_direct)
+    assert torch.equal(norms, n_direct)
