@@ -87,6 +87,27 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
   return (uint32_t)(((uint64_t)n * f.m) >> f.s);
 }
 
+// 1 / m_q for q = 0..BS-1 with a single division: prefix products, one
+// reciprocal of the full product, then one multiply-back per entry
+// (simultaneous inversion, Montgomery 1987).  In FP64 a division is a
+// multi-instruction sequence on the scarce FP64 units, so BS of them per
+// solve are worth folding into one.  The m_q are pivots of a nonsingular
+// block (|m_q| well inside 1e+-50, so the product stays in range).
+template <int BS>
+__device__ __forceinline__ void batch_recip(const double (&m)[BS], double (&inv)[BS]) {
+  double pre[BS];
+  pre[0] = m[0];
+#pragma unroll
+  for (int q = 1; q < BS; ++q) pre[q] = pre[q - 1] * m[q];
+  double r = 1.0 / pre[BS - 1];
+#pragma unroll
+  for (int q = BS - 1; q > 0; --q) {
+    inv[q] = r * pre[q - 1];
+    r *= m[q];
+  }
+  inv[0] = r;
+}
+
 // ----------------------------------------------- shifted Hessenberg solve
 //
 // Solve (H + i s I) y = b for an upper Hessenberg H (row-major BS x BS,
@@ -104,6 +125,23 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
 #pragma unroll
   for (int k = 0; k < BS - 1; ++k) tri = tri && (H[(k + 1) * BS + k] == TH(0));
   if (tri) {
+    // 1 / (d_k^2 + s^2): in FP64 one division for the whole block
+    T invs[BS];
+    if constexpr (sizeof(T) == 8) {
+      double m[BS];
+#pragma unroll
+      for (int k = 0; k < BS; ++k) {
+        const double d = (double)H[k * BS + k];
+        m[k] = d * d + s * s;
+      }
+      batch_recip<BS>(m, invs);
+    } else {
+#pragma unroll
+      for (int k = 0; k < BS; ++k) {
+        const T d = (T)H[k * BS + k];
+        invs[k] = recip(d * d + s * s);
+      }
+    }
 #pragma unroll
     for (int k = BS - 1; k >= 0; --k) {
       T ar = yr[k], ai = yi[k];
@@ -114,9 +152,8 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
         ai -= t * yi[c];
       }
       const T d = (T)H[k * BS + k];
-      const T inv = recip(d * d + s * s);
-      yr[k] = (ar * d + ai * s) * inv;
-      yi[k] = (ai * d - ar * s) * inv;
+      yr[k] = (ar * d + ai * s) * invs[k];
+      yi[k] = (ai * d - ar * s) * invs[k];
     }
     return;
   }

@@ -327,12 +327,16 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
   for (int q = 0; q < BS - 1; ++q) tri = tri && (H[(q + 1) * BS + q] == 0.0);
   double* xo = (double*)io.Xout + (size_t)i * R.K * 2 * BS;
   if (tri) {
+    double dg[BS], inv[BS];
+#pragma unroll
+    for (int q = 0; q < BS; ++q) dg[q] = H[q * BS + q];
+    batch_recip<BS>(dg, inv);  // one division for the block
 #pragma unroll
     for (int q = BS - 1; q >= 0; --q) {
       double acc = sr[q];
 #pragma unroll
       for (int c = q + 1; c < BS; ++c) acc -= H[q * BS + c] * sr[c];
-      sr[q] = acc / H[q * BS + q];
+      sr[q] = acc * inv[q];
     }
 #pragma unroll
     for (int t = 0; t < BS; ++t) reinterpret_cast<double2*>(xo)[t] = make_double2(sr[t], 0.0);
