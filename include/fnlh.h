@@ -199,7 +199,11 @@ int fnlh_build_jacobian(const fnlh_mesh *mesh, const double *Q, const fnlh_param
 
 /* Derived data for the sweeps: per node an orthogonal Q_i with
  * Q_i^T (J_ii + D_i I) Q_i upper Hessenberg, and the off-diagonal blocks
- * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags;
+ * rotated into that basis, Q_i^T J_ij Q_j, in the precisions of prep_flags.
+ * With b = 6 and frozen turbulence (column 5 zero in rows 0..4 of J_ii: the
+ * mean-flow equations do not see the turbulence variable) Q_i keeps that
+ * structure, and when every block has it the FP64 sweeps and the residual
+ * skip the structural zeros (fnlh_prep_structured tells);
  * with FNLH_PREP_TAGS the tagged column copy (from the mesh's periodic flags
  * and partition; FNLH_ERR_WORKSPACE when the mesh has either and the flag is
  * missing).  Depends only on J, D and the mesh, so it is
@@ -370,6 +374,12 @@ int fnlh_solve_ilu(const fnlh_mesh *mesh, const fnlh_jacobian *J, const fnlh_ilu
                    const double *omega, const double *sigma, const double *B, double *X, double tol,
                    int32_t max_iterations, int32_t flags, void *workspace, size_t workspace_bytes,
                    int32_t *iterations_done, double *rel_res, fnlh_stream_t stream);
+
+/* Whether fnlh_prepare certified the b = 6 frozen-turbulence zero pattern
+ * (every block, diagonal and off-diagonal, has column 5 zero in rows 0..4):
+ * *structured = 1 or 0.  FNLH_ERR_WORKSPACE without a prepared blob.
+ * SYNCHRONISING (reads one word of the blob). */
+int fnlh_prep_structured(const fnlh_jacobian *J, int32_t *structured, fnlh_stream_t stream);
 
 /* Timing hook (not part of the paper): when both are non-NULL, every later
  * relaxation on this host thread records `begin` on its stream right before

@@ -406,6 +406,20 @@ int fnlh_solve_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_ilu
                         iterations_done, rel_res, (cudaStream_t)stream);
 }
 
+int fnlh_prep_structured(const fnlh_jacobian* J, int32_t* structured, fnlh_stream_t stream) {
+  if (!J || !structured) return FNLH_ERR_ARG;
+  *structured = 0;
+  const int32_t* info = prep_info(J);
+  if (!info) return FNLH_ERR_WORKSPACE;
+  if (J->block != 6) return FNLH_OK;
+  int32_t h = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  FNLH_CUDA_TRY(cudaMemcpyAsync(&h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+  *structured = (h == 0) ? 1 : 0;
+  return FNLH_OK;
+}
+
 int fnlh_set_sweep_events(void* begin, void* end) {
   if ((begin == nullptr) != (end == nullptr)) return FNLH_ERR_ARG;
   set_sweep_events((cudaEvent_t)begin, (cudaEvent_t)end);

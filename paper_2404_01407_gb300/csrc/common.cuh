@@ -286,14 +286,18 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
 // rotf  [n][b][b] f32   Q_i in FP32 (same condition: the mixed solve's rotations)
 // offd64 / offd32 / offd16 [nnz][b][b] rotated off-diagonal copies
 // cols  [nnz] int32     col_idx with the passage and partition tags (FNLH_PREP_TAGS)
+// info  int32 words: [0] nonzero when the blocks do NOT have the frozen-
+//       turbulence zero pattern (see k_check_structure)
 struct PrepLayout {
-  size_t rot, hess, hessf, rotf, offd64, offd32, offd16, cols, total;
+  size_t info, rot, hess, hessf, rotf, offd64, offd32, offd16, cols, total;
 };
 
 inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) {
   PrepLayout p;
   const size_t bb = (size_t)b * b;
   size_t off = 0;
+  p.info = off;
+  off = 256;
   p.rot = off;
   off = align256(off + (size_t)n * bb * 8);
   p.hess = off;
@@ -326,6 +330,12 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
 }
 
 template <typename T> inline T* at(void* base, size_t off) { return reinterpret_cast<T*>((char*)base + off); }
+
+// The prepared blob's info word, or null (no prepared blob: nothing certified).
+inline const int32_t* prep_info(const fnlh_jacobian* J) {
+  if (!J->prep || !J->prep_ready) return nullptr;
+  return at<int32_t>(J->prep, prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags).info);
+}
 
 // The column array the sweeps and the residual read: the mesh's own, or on a
 // mesh with periodic edges or partitions the tagged copy in the prep blob (the

@@ -8,6 +8,8 @@
 // Both kernels here run once per nonlinear iteration, off the sweep loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "schur.cuh"
 
@@ -211,6 +213,58 @@ __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* 
       P[r][c] = diag[(size_t)i * BS * BS + r * BS + c] + (r == c ? Di : 0.0);
       Q[r][c] = (r == c) ? 1.0 : 0.0;
     }
+  if constexpr (BS == 6) {
+    // Frozen turbulence: the mean-flow rows do not see the turbulence
+    // variable (column 5 of rows 0..4 is zero), so M is block triangular once
+    // the turbulence variable comes first.  Its basis Z = [e_5 | (Z5; 0)],
+    // with Z5 the Schur (or Hessenberg) basis of the 5x5 mean-flow block,
+    // keeps that: every rotated block then has zeros below its first entry
+    // in column 0, which the FP64 kernels skip (k_check_structure certifies).
+    bool st = true;
+    for (int r = 0; r < 5; ++r) st = st && (P[r][5] == 0.0);
+    if (st) {
+      double P5[5][5], Q5[5][5];
+      for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) {
+          P5[r][c] = P[r][c];
+          Q5[r][c] = (r == c) ? 1.0 : 0.0;
+        }
+      hessenberg_reduce<5>(P5, Q5);
+      double T5[5][5], Z5[5][5];
+      for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) {
+          T5[r][c] = P5[r][c];
+          Z5[r][c] = Q5[r][c];
+        }
+      const bool tri5 = schur_real<5>(T5, Z5);
+      double Z6[6][6], H6[6][6];
+      for (int m = 0; m < 6; ++m)
+        for (int c = 0; c < 6; ++c) {
+          Z6[m][c] = (c == 0) ? (m == 5 ? 1.0 : 0.0) : (m < 5 ? (tri5 ? Z5[m][c - 1] : Q5[m][c - 1]) : 0.0);
+          H6[m][c] = 0.0;
+        }
+      H6[0][0] = P[5][5];
+      for (int c = 1; c < 6; ++c) {
+        double t = 0.0;
+        for (int m = 0; m < 5; ++m) t += P[5][m] * Z6[m][c];
+        H6[0][c] = t;
+      }
+      for (int r = 1; r < 6; ++r)
+        for (int c = 1; c < 6; ++c) {
+          const double v = tri5 ? T5[r - 1][c - 1] : P5[r - 1][c - 1];
+          H6[r][c] = tri5 ? ((r > c) ? 0.0 : v) : ((r > c + 1) ? 0.0 : v);
+        }
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+          const size_t o = (size_t)i * 36 + r * 6 + c;
+          rot[o] = Z6[r][c];
+          if (rotf) rotf[o] = (float)Z6[r][c];
+          hess[o] = H6[r][c];
+          if (hessf) hessf[o] = (float)H6[r][c];
+        }
+      return;
+    }
+  }
   hessenberg_reduce<BS>(P, Q);
   double T[BS][BS], Z[BS][BS];
   for (int r = 0; r < BS; ++r)
@@ -301,6 +355,21 @@ __global__ void __launch_bounds__(128) k_tag_columns(int32_t n, const int32_t* _
   }
 }
 
+// Certifies the frozen-turbulence zero pattern (b = 6) that the FP64 kernels
+// exploit: every node's basis has e_5 as its first column (so its M had
+// column 5 zero above the diagonal) and every off-diagonal block has column 5
+// zero in rows 0..4.  Any violation sets info[0]; thread t checks node t and
+// CSR entry t.
+__global__ void __launch_bounds__(128) k_check_structure(int32_t n, int32_t nnz, const double* __restrict__ offd,
+                                                         const double* __restrict__ rot, int32_t* __restrict__ info) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (t < n) bad = rot[(size_t)t * 36 + 5 * 6 + 0] != 1.0;
+  if (t < nnz)
+    for (int r = 0; r < 5; ++r) bad = bad || (offd[(size_t)t * 36 + r * 6 + 5] != 0.0);
+  if (bad) atomicOr(info, 1);
+}
+
 template <int BS>
 int launch_build(const BuildArgs& a, cudaStream_t s) {
   if (a.n == 0) return FNLH_OK;
@@ -319,6 +388,13 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   const int n = J->n_nodes;
   if (n > 0) {
     k_prepare_basis<BS><<<(n + 127) / 128, 128, 0, s>>>(n, J->diag, J->D, rot, hess, hessf, rotf);
+    FNLH_LAUNCH_CHECK();
+  }
+  int32_t* info = at<int32_t>(J->prep, L.info);
+  // nonzero bytes: no pattern to exploit (b = 5), cleared for b = 6 before the check
+  FNLH_CUDA_TRY(cudaMemsetAsync(info, BS == 6 ? 0 : 1, sizeof(int32_t), s));
+  if (BS == 6 && std::max(n, J->nnz) > 0) {
+    k_check_structure<<<(std::max(n, J->nnz) + 127) / 128, 128, 0, s>>>(n, J->nnz, J->offd, rot, info);
     FNLH_LAUNCH_CHECK();
   }
   double* o64 = (L.offd64 != (size_t)-1) ? at<double>(J->prep, L.offd64) : nullptr;

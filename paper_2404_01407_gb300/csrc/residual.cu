@@ -31,6 +31,7 @@ struct ResArgs {
   double* r;        // nullable [n][C][b]
   float* r32rot;    // nullable [n][K][b] complex: Q_i^T r_i in FP32 (r rounded to FP32 first)
   const float* rotf;  // Q_i in FP32 (with r32rot)
+  const int32_t* info;  // prep info word, nullable: 0 = the b = 6 frozen-turbulence pattern holds
   int32_t x_zero;     // x is zero: r = B without reading X
   double* partials; // [gridDim][2K]
   Systems sys;
@@ -53,6 +54,9 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
     ri[t] = bi[t];
   }
   const int p0 = a.row_ptr[i], p1 = a.x_zero ? p0 : a.row_ptr[i + 1];
+  // frozen turbulence (original basis): rows 0..4 of every block skip column 5
+  bool pattern = false;
+  if constexpr (BS == 6) pattern = a.info != nullptr && __ldg(a.info) == 0;
   if (cplx) {
     for (int p = p0; p < p1; ++p) {
       const int cj = a.col_idx[p];
@@ -65,14 +69,25 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
       }
       if (side_of(cj)) phase_shift<BS, double>(xr, xi, side_of(cj), a.sys.phase[k]);
       const double* J = a.offd + (size_t)p * BS * BS;
+      if (pattern) {
 #pragma unroll
-      for (int q = 0; q < BS; ++q)
+        for (int q = 0; q < BS; ++q)
 #pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          const double jv = __ldg(J + q * BS + t);
-          rr[q] -= jv * xr[t];
-          ri[q] -= jv * xi[t];
-        }
+          for (int t = 0; t < ((q < BS - 1) ? BS - 1 : BS); ++t) {
+            const double jv = __ldg(J + q * BS + t);
+            rr[q] -= jv * xr[t];
+            ri[q] -= jv * xi[t];
+          }
+      } else {
+#pragma unroll
+        for (int q = 0; q < BS; ++q)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) {
+            const double jv = __ldg(J + q * BS + t);
+            rr[q] -= jv * xr[t];
+            ri[q] -= jv * xi[t];
+          }
+      }
     }
   } else {
     for (int p = p0; p < p1; ++p) {
@@ -82,10 +97,17 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
 #pragma unroll
       for (int t = 0; t < BS; ++t) xr[t] = __ldg(xj + t);
       const double* J = a.offd + (size_t)p * BS * BS;
+      if (pattern) {
 #pragma unroll
-      for (int q = 0; q < BS; ++q)
+        for (int q = 0; q < BS; ++q)
 #pragma unroll
-        for (int t = 0; t < BS; ++t) rr[q] -= __ldg(J + q * BS + t) * xr[t];
+          for (int t = 0; t < ((q < BS - 1) ? BS - 1 : BS); ++t) rr[q] -= __ldg(J + q * BS + t) * xr[t];
+      } else {
+#pragma unroll
+        for (int q = 0; q < BS; ++q)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) rr[q] -= __ldg(J + q * BS + t) * xr[t];
+      }
     }
   }
   // diagonal block, D and the spectral term i omega V
@@ -229,6 +251,7 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   a.r = r;
   a.r32rot = r32rot;
   a.rotf = rotf;
+  a.info = prep_info(J);
   a.x_zero = x_zero;
   a.partials = at<double>(ws, W.partials);
   a.sys = sys;
@@ -298,6 +321,7 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   a.r = r;
   a.r32rot = nullptr;
   a.rotf = nullptr;
+  a.info = prep_info(J);
   a.x_zero = 0;
   a.partials = partials;
   a.sys = sys;

@@ -193,11 +193,13 @@ struct SweepOperands {
   const double* rot;
   const float* rotf;    // FP32 basis (low-precision sweeps only)
   const int32_t* cols;  // column indices (passage-tagged on a periodic mesh)
+  const int32_t* info;  // prep info word (frozen-turbulence pattern)
 };
 
 int sweep_operands(const fnlh_mesh* m, const fnlh_jacobian* J, int precision, SweepOperands* o) {
   const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
   o->cols = csr_columns(m, J);
+  o->info = at<int32_t>(J->prep, L.info);
   o->rot = at<double>(J->prep, L.rot);
   o->rotf = (L.rotf != (size_t)-1) ? at<float>(J->prep, L.rotf) : nullptr;
   if (precision == FNLH_F64) {
@@ -301,6 +303,7 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.row.hess = op.hess;
   a.row.vol = m->vol;
   a.row.Bt = Bt;
+  a.row.info = op.info;
   a.status = status;
   a.masked = active ? 1 : 0;
   a.active[0] = active ? active[0] : ~0ull;
@@ -615,6 +618,7 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
     D.row.hess = P.ops[r].hess;
     D.row.vol = R.mesh->vol;
     D.row.Bt = base + W.vec[0];
+    D.row.info = P.ops[r].info;
     D.x[0] = base + W.vec[1];
     D.x[1] = base + W.vec[2];
     D.tile0 = tiles;

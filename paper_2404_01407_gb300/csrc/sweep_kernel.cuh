@@ -219,7 +219,45 @@ struct TileRow {
   const void* hess;  // [n][b][b] (double for FP64 sweeps, float otherwise)
   const double* vol;
   const void* Bt;    // [n][K][b] complex, right-hand side in the rotated basis
+  const int32_t* info;  // prep info word: 0 = the b = 6 frozen-turbulence pattern holds (FP64 skips its zeros)
 };
+
+// b = 6 with the frozen-turbulence pattern certified by fnlh_prepare: in the
+// rotated basis column 0 of every off-diagonal block is zero below row 0.
+template <int BS>
+__device__ __forceinline__ bool frozen_turbulence(const TileRow& R) {
+  if constexpr (BS == 6) return R.info != nullptr && __ldg(R.info) == 0;
+  else return false;
+}
+
+// s -= J x for one FP64 block (complex slice); with the pattern, rows 1..5
+// skip their structurally zero column 0.
+template <int BS>
+__device__ __forceinline__ void spmv_block_f64(const double (&J)[BS * BS], const Cvec<BS, double>& x,
+                                               Cvec<BS, double>& s, bool pattern) {
+  if (pattern) {
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      s.re[0] -= J[t] * x.re[t];
+      s.im[0] -= J[t] * x.im[t];
+    }
+#pragma unroll
+    for (int r = 1; r < BS; ++r)
+#pragma unroll
+      for (int t = 1; t < BS; ++t) {
+        s.re[r] -= J[r * BS + t] * x.re[t];
+        s.im[r] -= J[r * BS + t] * x.im[t];
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int t = 0; t < BS; ++t) {
+        s.re[r] -= J[r * BS + t] * x.re[t];
+        s.im[r] -= J[r * BS + t] * x.im[t];
+      }
+  }
+}
 
 // The iterate buffers and frequencies of one launch (the row descriptor
 // itself is read in place from the kernel parameters).
@@ -256,8 +294,8 @@ __device__ __forceinline__ void finish_pair(const TileRow& R, const SweepIO& io,
 }
 
 // FP64 (or unstaged) form: blocks and factors straight from global memory.
-template <int BS>
-__device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& io, long long g, bool x_zero) {
+template <int BS, bool kPattern>
+__device__ __forceinline__ void sweep_pair_f64_body(const TileRow& R, const SweepIO& io, long long g, bool x_zero) {
   const int i = (int)fdiv((uint32_t)g, R.divK);
   const int k = (int)g - i * R.K;
   Cvec<BS, double> s;
@@ -274,16 +312,16 @@ __device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& 
       if (side_of(cj)) phase_shift<BS, double>(x.re, x.im, side_of(cj), io.phase[k]);
       double J[BS * BS];
       load_block<BS>(offd + (size_t)p * BS * BS, J);
-#pragma unroll
-      for (int r = 0; r < BS; ++r)
-#pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          s.re[r] -= J[r * BS + t] * x.re[t];
-          s.im[r] -= J[r * BS + t] * x.im[t];
-        }
+      spmv_block_f64<BS>(J, x, s, kPattern);
     }
   }
   finish_pair<BS, double>(R, io, (const double*)R.hess + (size_t)i * BS * BS, i, k, s);
+}
+
+template <int BS>
+__device__ __forceinline__ void sweep_pair_f64(const TileRow& R, const SweepIO& io, long long g, bool x_zero) {
+  if (frozen_turbulence<BS>(R)) sweep_pair_f64_body<BS, true>(R, io, g, x_zero);
+  else sweep_pair_f64_body<BS, false>(R, io, g, x_zero);
 }
 
 // FP64, system-major tile: a CTA owns 32 consecutive nodes and each warp
@@ -304,6 +342,7 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
   if (!x_zero) {
     const double* __restrict__ X = (const double*)io.Xin;
     const double* __restrict__ offd = (const double*)R.offd;
+    const bool pattern = frozen_turbulence<BS>(R);
     const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
     for (int p = p0; p < p1; ++p) {
       const int cj = __ldg(R.col_idx + p);
@@ -315,10 +354,19 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
       for (int t = 0; t < BS; ++t) xr[t] = __ldg(xs + 2 * t);
       double J[BS * BS];
       load_block<BS>(offd + (size_t)p * BS * BS, J);
+      if (pattern) {
 #pragma unroll
-      for (int r = 0; r < BS; ++r)
+        for (int t = 0; t < BS; ++t) sr[0] -= J[t] * xr[t];
 #pragma unroll
-        for (int t = 0; t < BS; ++t) sr[r] -= J[r * BS + t] * xr[t];
+        for (int r = 1; r < BS; ++r)
+#pragma unroll
+          for (int t = 1; t < BS; ++t) sr[r] -= J[r * BS + t] * xr[t];
+      } else {
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) sr[r] -= J[r * BS + t] * xr[t];
+      }
     }
   }
   const double* H = (const double*)R.hess + (size_t)i * BS * BS;

@@ -110,6 +110,7 @@ _SIGS = {
                                           ctypes.POINTER(fnlh_tuning), c_vp, c_sz, ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32), ctypes.POINTER(c_f64), c_vp]),
     "fnlh_set_sweep_events": (ctypes.c_int, [c_vp, c_vp]),
+    "fnlh_prep_structured": (ctypes.c_int, [ctypes.POINTER(fnlh_jacobian), ctypes.POINTER(c_i32), c_vp]),
     "fnlh_mesh_color": (ctypes.c_int, [c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, ctypes.POINTER(c_i32)]),
     "fnlh_ilu_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
     "fnlh_ilu_factor": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_i32,
@@ -392,6 +393,13 @@ def fnlh_solve_batched(batch: BatchedRows, precision, tol, inner_sweeps, max_che
     if raise_on_error and st != FNLH_OK:
         raise FnlhError(st, "fnlh_solve_batched")
     return st, checks.value, sweeps.value, np.array(rel[:])
+
+
+def fnlh_prep_structured(J, stream=None) -> bool:
+    """Whether fnlh_prepare certified the b = 6 frozen-turbulence zero pattern."""
+    v = c_i32(0)
+    _check(lib().fnlh_prep_structured(ctypes.byref(J.c), ctypes.byref(v), _stream(stream)), "fnlh_prep_structured")
+    return bool(v.value)
 
 
 def fnlh_set_sweep_events(begin=None, end=None):

@@ -415,3 +415,29 @@ def test_relax_and_residual_capture_in_a_cuda_graph():
     torch.cuda.synchronize()
     assert torch.equal(X, X_direct)
     assert torch.equal(norms, n_direct)
+
+
+def test_frozen_turbulence_pattern_is_certified_and_optional():
+    """b = 6: the build's blocks have the frozen-turbulence zeros, fnlh_prepare
+    certifies them and the FP64 kernels skip them; a Jacobian without the
+    pattern is relaxed densely, both at 1e-12 of the oracle.  b = 5 has no
+    pattern."""
+    p = small("b6n4")
+    dm, J, B = _gpu.device_problem(p)
+    assert fnlh.fnlh_prep_structured(J)
+    oj = _gpu.oracle_jacobian(p)
+    # one off-diagonal block couples a mean-flow row to the turbulence variable
+    oj.offd[3][0, 5] = 0.05 * np.abs(oj.offd[3]).max()
+    _gpu.load_jacobian(dm, J, oj)
+    assert not fnlh.fnlh_prep_structured(J)
+    X = torch.zeros_like(B)
+    fnlh.fnlh_relax(dm, J, p.omega, B, X, 25, fnlh.FNLH_F64)
+    ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 25)
+    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+    assert np.all(err <= 1e-12), err
+    x = np.random.default_rng(2).normal(size=p.b.shape)
+    norms = fnlh.fnlh_residual(dm, J, p.omega, B, torch.from_numpy(x).cuda()).cpu().numpy()
+    on, _ = oracle.residual(oj, p.mesh.vol, p.omega, p.b, x)
+    assert np.allclose(norms, on, rtol=1e-12, atol=0)
+    d5, J5, _ = _gpu.device_problem(small("c1"))
+    assert not fnlh.fnlh_prep_structured(J5)
