@@ -44,7 +44,7 @@ struct SweepArgs {
 // FP64: a CTA per 32 consecutive nodes, each warp taking whole systems for
 // them (system-major), so that the mean flow's warp runs the real-only path.
 template <int BS>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_f64(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_f64(const __grid_constant__ SweepArgs a) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   if (i >= a.row.n) return;
   const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr, a.phase};
