@@ -187,21 +187,30 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
   }
 }
 
-// One block walks tiles of 32 nodes (grid stride); within a tile each warp
-// takes whole systems (lane = node), reduces them with a fixed shuffle tree
-// and adds them, in tile order, to the block's per-system sums -- one writer
-// per system per tile, so the result is bit-reproducible.
+// One block walks tiles of 32 nodes (grid stride), kResidualRound tiles at a
+// time: the round's (tile, system) items are dealt round-robin to the warps
+// (lane = node), each reduced by a fixed shuffle tree into its own shared
+// slot; then the slots are added to the block's per-system sums in tile
+// order.  The work is balanced whatever K (the mean flow's real items cost
+// half) and the sums are added in the same order as one writer per system
+// would, so the result is bit-reproducible.
+constexpr int kResidualRound = 8;
+
 template <int BS>
 __global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_constant__ ResArgs a) {
   __shared__ double s_acc[2 * kMaxSys];
+  __shared__ double s_item[kResidualRound][2 * kMaxSys];
   const int K = a.sys.K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) s_acc[t] = 0.0;
   __syncthreads();
   const int tiles = (a.n + 31) / 32;
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int i = tile * 32 + lane;
-    for (int k = warp; k < K; k += nwarps) {
+  const int mine = (tiles > (int)blockIdx.x) ? (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  for (int m0 = 0; m0 < mine; m0 += kResidualRound) {
+    const int rcount = min(kResidualRound, mine - m0);
+    for (int it = warp; it < rcount * K; it += nwarps) {
+      const int tl = it / K, k = it - tl * K;
+      const int i = ((int)blockIdx.x + (m0 + tl) * (int)gridDim.x) * 32 + lane;
       double rs = 0.0, bs = 0.0;
       if (i < a.n) residual_pair<BS>(a, i, k, rs, bs);
 #pragma unroll
@@ -210,12 +219,15 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_cons
         bs += __shfl_xor_sync(0xffffffffu, bs, off);
       }
       if (lane == 0) {
-        s_acc[2 * k] += rs;
-        s_acc[2 * k + 1] += bs;
+        s_item[tl][2 * k] = rs;
+        s_item[tl][2 * k + 1] = bs;
       }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * K; t += blockDim.x)
+      for (int tl = 0; tl < rcount; ++tl) s_acc[t] += s_item[tl][t];
+    __syncthreads();
   }
-  __syncthreads();
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) a.partials[(size_t)blockIdx.x * 2 * K + t] = s_acc[t];
 }
 
@@ -256,7 +268,7 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   a.partials = at<double>(ws, W.partials);
   a.sys = sys;
   const int grid = residual_grid(a.n);
-  const int threads = 32 * std::min(sys.K, kResidualThreads / 32);
+  const int threads = kResidualThreads;
   if (J->block == 5) k_residual<5><<<grid, threads, 0, s>>>(a);
   else k_residual<6><<<grid, threads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
@@ -325,7 +337,7 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   a.x_zero = 0;
   a.partials = partials;
   a.sys = sys;
-  const int threads = 32 * std::min(sys.K, kResidualThreads / 32);
+  const int threads = kResidualThreads;
   if (J->block == 5) k_residual<5><<<grid, threads, 0, s>>>(a);
   else k_residual<6><<<grid, threads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
