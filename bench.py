@@ -377,7 +377,9 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
     X = torch.zeros_like(B)
     ws = fnlh.workspace(n, b, N, dev)
     out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, b=6, mean + {N} harmonics, CFL 20, tol {tol:g}"}
-    cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 12)]
+    # inner sweeps per FP64 residual: the best of a scan of 10..40 on this workload (every run needs
+    # ~60 sweeps; each extra check costs one FP64 residual)
+    cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)]
     zg = fnlh.FNLH_SOLVE_ZERO_GUESS
     for name, prec, inner in cases:
         fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)  # warm
@@ -643,10 +645,10 @@ def large_section(torch, fnlh, inputs, dev, tol=1e-8):
         ws = fnlh.workspace(n, 6, N, dev, precision=fnlh.FNLH_BF16)
         om = inputs.omegas(N)
         zg = fnlh.FNLH_SOLVE_ZERO_GUESS
-        fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 12, 1, ws=ws, raise_on_error=False, flags=zg)
+        fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 25, 1, ws=ws, raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 12, 200, ws=ws,
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 25, 200, ws=ws,
                                                   raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
@@ -740,7 +742,7 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         sw = fn()
         torch.cuda.synchronize()
         solves[name] = {"seconds": time.perf_counter() - t0, "max_sweeps": sw}
-    for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 12)):
+    for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)):
         sb = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
         sws = torch.empty(sb.workspace_bytes(6, pc), dtype=torch.uint8, device=dev)
         fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
