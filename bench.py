@@ -381,6 +381,7 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
     # ~60 sweeps; each extra check costs one FP64 residual)
     cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)]
     zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    x64 = None
     for name, prec, inner in cases:
         fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)  # warm
         torch.cuda.synchronize()
@@ -390,7 +391,16 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         out[name] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
-                     "inner_sweeps": inner, "max_rel_residual": float(np.max(rel))}
+                     "inner_sweeps": inner, "max_rel_residual": float(np.max(rel)),
+                     "rel_residual_per_system": [float(v) for v in rel]}
+        # per-system error against the FP64 solution (itself at 1e-12 of the oracle), both at 1e-8 residual
+        if x64 is None:
+            x64 = X.clone()
+        else:
+            cols = [[0]] + [[2 * k - 1, 2 * k] for k in range(1, N + 1)]
+            out[name]["rel_error_vs_fp64_per_system"] = [
+                float(torch.linalg.vector_norm(X[:, c] - x64[:, c]) / torch.linalg.vector_norm(x64[:, c]))
+                for c in cols]
     if out["f64"]["status"] == "success":
         for name in ("f32", "bf16"):
             out[name]["speedup_vs_f64"] = out["f64"]["seconds"] / out[name]["seconds"]
@@ -401,7 +411,9 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
         ms = sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec)
         alg = sweep_bytes(n, nnz, b, N, sj, 4, 4, 4)
         out[name]["inner_sweep"] = {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
-                                    "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+                                    "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                                    "frac_hbm_nominal_7900": alg / (ms * 1e-3) / 1e9 / 7900.0}
+    del x64
     return out
 
 
