@@ -175,9 +175,21 @@ def cpu_oracle_rate(p, budget_s=15.0, max_sweeps=30):
     oracle.residual(oj, m.vol, p.omega, p.b, X)
     t = time.perf_counter() - t0
     K = 1 + p.n_harm
-    return {"value": m.n_nodes * K * S / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one thread, over fewer sweeps
+    oracle.set_num_threads(1)
+    try:
+        S1 = max(1, min(3, S))
+        t0 = time.perf_counter()
+        oracle.jacobi(oj, m.vol, p.omega, p.b, S1, X0=X)
+        t_1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": m.n_nodes * K * S / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{p.name} full mesh, {S} FP64 Jacobi sweeps + 1 residual after 1 warm sweep "
-                      f"(build {t_build:.1f} s excluded), {t:.1f} s"}
+                      f"(build {t_build:.1f} s excluded), {t:.1f} s",
+            "single_thread": {"value": m.n_nodes * K * S1 / t_1, "unit": UNIT, "cores": 1,
+                              "sample": f"{S1} FP64 Jacobi sweeps, {t_1:.1f} s"}}
 
 
 def run_reference(args):

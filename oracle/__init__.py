@@ -95,6 +95,8 @@ def _bind(lib):
     lib.oracle_ilu_apply.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_void_p, _i32p, _f64p, _f64p,
                                      _f64p, _f64p]
     lib.oracle_ilu_apply.restype = ctypes.c_int
+    lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_num_threads.restype = None
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
     return lib
@@ -119,6 +121,11 @@ def restore_library(handle):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's row loops (timing only; results do not depend on it)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def _f64(a):

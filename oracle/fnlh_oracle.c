@@ -682,6 +682,15 @@ int oracle_ilu_apply(int n, int b, const int32_t *row_ptr, const int32_t *col_id
     return fail ? -1 : 0;
 }
 
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
