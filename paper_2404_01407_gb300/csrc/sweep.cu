@@ -8,7 +8,10 @@
 //
 // Design (GB300): one thread per (node, system); the off-diagonal product is
 // accumulated in registers and the shifted diagonal system solved in
-// registers.  The sweeps run in the per-node Hessenberg basis prepared by
+// registers.  FP64: a CTA owns 32 nodes and each warp whole systems for them
+// (the mean flow's warp runs a real-only path).  FP32/BF16: 128-pair tiles
+// whose blocks are staged in shared memory when a node serves enough systems.
+// The sweeps run in the per-node Hessenberg basis prepared by
 // fnlh_prepare (x = Q x~), where the diagonal block of system k is
 // H_i + i omega_k V_i I and its solve costs O(b^2).  Iterates live in the
 // internal complex-interleaved layout [n][K][b]; the rotate kernels move

@@ -400,11 +400,9 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
   }
 }
 
-// Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
-// Every thread of the CTA must call it (it synchronises).
 // s -= J x for one staged FP32 block, consumed row by row from shared
 // memory: six live block entries instead of thirty-six keep the register
-// count (and with it three CTAs per SM) without spilling.
+// count (64, eight CTAs per SM) without spilling.
 template <int BS>
 __device__ __forceinline__ void spmv_rows_smem(const float* jb, const Cvec<BS, float>& x, Cvec<BS, float>& s) {
 #pragma unroll
@@ -466,6 +464,7 @@ __device__ __forceinline__ void spmv_rows_global(const TJ* __restrict__ jb, cons
   }
 }
 
+// Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
 // Every thread of the CTA must call this (it synchronises).
 template <int BS, typename TJ>
 __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& io, long long g0, bool x_zero,
