@@ -274,7 +274,9 @@ def run_fnlh(args):
         fnlh.fnlh_residual(dm, J, p.omega, B, X, norms=norms, ws=ws)
 
     # kernels launched per step: build, hessenberg, rotate_offd, 2 rotate_in, sweeps, rotate_out, residual, reduce
-    launches_per_step = 3 + 2 + SWEEPS + 1 + 2
+    # build, basis, pattern check, block rotation; rotate B and X in; the sweeps;
+    # rotate out; residual + its reduction (the ncu launch list shows the same count)
+    launches_per_step = 4 + 2 + SWEEPS + 1 + 2
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
