@@ -276,7 +276,7 @@ def run_fnlh(args):
     # kernels launched per step: build, hessenberg, rotate_offd, 2 rotate_in, sweeps, rotate_out, residual, reduce
     # build, basis, pattern check, block rotation; rotate B and X in; the sweeps;
     # rotate out; residual + its reduction (the ncu launch list shows the same count)
-    launches_per_step = 4 + 2 + SWEEPS + 1 + 2
+    launches_per_step = (4 if p.block == 6 else 3) + 2 + SWEEPS + 1 + 2
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
