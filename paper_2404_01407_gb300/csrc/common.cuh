@@ -117,8 +117,11 @@ __device__ __forceinline__ void batch_recip(const double (&m)[BS], double (&inv)
 // (yr, yi) holds b on entry and y on return.  Cost O(BS^2) complex
 // operations instead of the O(BS^3) of a general block LU.  H may point to
 // global or shared memory (plain loads).
+// pivinv (nullable, FP64): the precomputed 1 / (d_k^2 + s^2) of this block and
+// shift, so that no division is left in the solve.
 template <int BS, typename T, typename TH>
-__device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr)[BS], T (&yi)[BS]) {
+__device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr)[BS], T (&yi)[BS],
+                                           const T* __restrict__ pivinv = nullptr) {
   // Triangular factor (real Schur form, every subdiagonal exactly zero):
   // plain back-substitution, y_k = (b_k - sum_{c>k} T_kc y_c) / (T_kk + i s).
   bool tri = true;
@@ -127,7 +130,10 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
   if (tri) {
     // 1 / (d_k^2 + s^2): in FP64 one division for the whole block
     T invs[BS];
-    if constexpr (sizeof(T) == 8) {
+    if (pivinv) {
+#pragma unroll
+      for (int k = 0; k < BS; ++k) invs[k] = pivinv[k];
+    } else if constexpr (sizeof(T) == 8) {
       double m[BS];
 #pragma unroll
       for (int k = 0; k < BS; ++k) {
@@ -255,8 +261,9 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
 // [256, +partials)              residual partial sums  kResidualGrid x 2K doubles
 // norms                         final 2K doubles of the last residual
 // vec0, vec1, vec2              three [n][K][b] complex vectors (internal layout) in the precision's type
+// pivinv                        FP64 only: [n][K][b] reciprocal pivots of the shifted triangular solves
 struct WsLayout {
-  size_t status, partials, norms, vec[3], total, vec_bytes;
+  size_t status, partials, norms, vec[3], pivinv, total, vec_bytes;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -273,6 +280,11 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
   for (int v = 0; v < 3; ++v) {
     w.vec[v] = off;
     off = align256(off + w.vec_bytes);
+  }
+  w.pivinv = (size_t)-1;
+  if (precision == FNLH_F64) {
+    w.pivinv = off;
+    off = align256(off + (size_t)n * K * block * sizeof(double));
   }
   w.total = off;
   return w;

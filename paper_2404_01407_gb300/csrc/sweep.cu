@@ -171,6 +171,48 @@ static inline unsigned blocks_for(long long count, int threads) {
   return (unsigned)((count + threads - 1) / threads);
 }
 
+struct PivotArgs {
+  long long count;  // n K
+  int32_t K;
+  const double* hess;
+  const double* vol;
+  double* out;      // [n][K][b]
+  double omega[kMaxSys];
+};
+
+// Reciprocal pivots of every (node, system) triangular solve, once per call:
+// the sweeps then divide nowhere (an FP64 division is a multi-instruction
+// sequence on GB300's scarce FP64 units).  Mean flow: 1 / d_q; harmonic k:
+// 1 / (d_q^2 + (omega_k V_i)^2) with d_q the diagonal of the Schur factor.
+template <int BS>
+__global__ void __launch_bounds__(256) k_pivot_inverses(const __grid_constant__ PivotArgs a) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.count) return;
+  const long long i = g / a.K;
+  const int k = (int)(g - i * a.K);
+  const double s = a.omega[k] * a.vol[i];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    const double d = a.hess[(size_t)i * BS * BS + q * BS + q];
+    a.out[(size_t)g * BS + q] = (k == 0) ? 1.0 / d : 1.0 / (d * d + s * s);
+  }
+}
+
+template <int BS>
+static int pivot_inverses(const fnlh_mesh* m, const double* hess, const Systems& sys, double* out, cudaStream_t s) {
+  PivotArgs a;
+  a.count = (long long)m->n_nodes * sys.K;
+  if (a.count == 0) return FNLH_OK;
+  a.K = sys.K;
+  a.hess = hess;
+  a.vol = m->vol;
+  a.out = out;
+  for (int k = 0; k < kMaxSys; ++k) a.omega[k] = sys.omega[k];
+  k_pivot_inverses<BS><<<blocks_for(a.count, 256), 256, 0, s>>>(a);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
 template <int BS, typename TO>
 int rotate_in(int n, int K, const double* rot, const double* x, TO* y, cudaStream_t s) {
   const long long count = (long long)n * K;
@@ -293,7 +335,7 @@ int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
 template <int BS, typename TJ, typename T>
 int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, const T* Bt, T* x0, T* x1,
                int sweeps, int x_zero, int32_t* status, cudaStream_t s, T** result,
-               const uint64_t* active = nullptr) {
+               const uint64_t* active = nullptr, const double* pivinv = nullptr) {
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.row.n = m->n_nodes;
@@ -307,6 +349,7 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.row.vol = m->vol;
   a.row.Bt = Bt;
   a.row.info = op.info;
+  a.row.pivinv = pivinv;
   a.status = status;
   a.masked = active ? 1 : 0;
   a.active[0] = active ? active[0] : ~0ull;
@@ -352,7 +395,13 @@ int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   if ((rc = rotate_in<BS, T>(n, sys.K, op.rot, B, bt, s))) return rc;
   if ((rc = rotate_in<BS, T>(n, sys.K, op.rot, X, x0, s))) return rc;
   T* res = x0;
-  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, at<int32_t>(ws, W.status), s, &res)))
+  double* pivinv = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    pivinv = at<double>(ws, W.pivinv);
+    if ((rc = pivot_inverses<BS>(m, (const double*)op.hess, sys, pivinv, s))) return rc;
+  }
+  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, at<int32_t>(ws, W.status), s, &res, nullptr,
+                                  pivinv)))
     return rc;
   return rotate_out<BS, T>(n, sys.K, op.rot, res, X, 0, s);
 }
@@ -433,6 +482,11 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     if ((rc = rotate_in<BS, T>(n, K, op.rot, X, v1, s))) return rc;
   }
   T* cur = v1;
+  double* pivinv = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    pivinv = at<double>(ws, W.pivinv);
+    if ((rc = pivot_inverses<BS>(m, (const double*)op.hess, sys, pivinv, s))) return rc;
+  }
   FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   for (;;) {
     // mixed: Q^T r in FP32 straight into v0; FP64 defect correction: r into v2
@@ -461,7 +515,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       if constexpr (sizeof(T) == 8) {
         if ((rc = rotate_in<BS, T>(n, K, op.rot, (const double*)v2, v0, s))) return rc;
       }
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res, act))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res, act, pivinv))) return rc;
       const long long count = (long long)n * K;
       if constexpr (sizeof(T) == 4) {
         if (count > 0) {
@@ -473,7 +527,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       }
     } else {
       T* other = (cur == v1) ? v2 : v1;
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res, act))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res, act, pivinv))) return rc;
       cur = res;
       if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 0, s))) return rc;
     }
@@ -622,6 +676,7 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
     D.row.vol = R.mesh->vol;
     D.row.Bt = base + W.vec[0];
     D.row.info = P.ops[r].info;
+    D.row.pivinv = nullptr;  // the batched FP64 tile divides in place
     D.x[0] = base + W.vec[1];
     D.x[1] = base + W.vec[2];
     D.tile0 = tiles;

@@ -220,6 +220,10 @@ struct TileRow {
   const double* vol;
   const void* Bt;    // [n][K][b] complex, right-hand side in the rotated basis
   const int32_t* info;  // prep info word: 0 = the b = 6 frozen-turbulence pattern holds (FP64 skips its zeros)
+  // nullable, FP64: [n][K][b] reciprocal pivots (k = 0: 1 / d_q; k > 0: 1 / (d_q^2 + s_k^2)).
+  // Set only for the single-row kernel, whose mean flow takes the real path,
+  // so the complex solve reads it for k > 0 alone.
+  const double* pivinv;
 };
 
 // b = 6 with the frozen-turbulence pattern certified by fnlh_prepare: in the
@@ -289,7 +293,10 @@ template <int BS, typename T, typename TH>
 __device__ __forceinline__ void finish_pair(const TileRow& R, const SweepIO& io, const TH* H, int i, int k,
                                             Cvec<BS, T>& s) {
   const T shift = (T)(io.omega[k] * __ldg(R.vol + i));
-  hess_solve<BS, T>(H, shift, s.re, s.im);
+  if constexpr (sizeof(T) == 8)
+    hess_solve<BS, T>(H, shift, s.re, s.im, R.pivinv ? R.pivinv + ((size_t)i * R.K + k) * BS : nullptr);
+  else
+    hess_solve<BS, T>(H, shift, s.re, s.im);
   store_slice<BS>((T*)io.Xout + ((size_t)i * R.K + k) * 2 * BS, s);
 }
 
@@ -375,10 +382,16 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
   for (int q = 0; q < BS - 1; ++q) tri = tri && (H[(q + 1) * BS + q] == 0.0);
   double* xo = (double*)io.Xout + (size_t)i * R.K * 2 * BS;
   if (tri) {
-    double dg[BS], inv[BS];
+    double inv[BS];
+    if (R.pivinv) {
 #pragma unroll
-    for (int q = 0; q < BS; ++q) dg[q] = H[q * BS + q];
-    batch_recip<BS>(dg, inv);  // one division for the block
+      for (int q = 0; q < BS; ++q) inv[q] = __ldg(R.pivinv + (size_t)i * R.K * BS + q);
+    } else {
+      double dg[BS];
+#pragma unroll
+      for (int q = 0; q < BS; ++q) dg[q] = H[q * BS + q];
+      batch_recip<BS>(dg, inv);  // one division for the block
+    }
 #pragma unroll
     for (int q = BS - 1; q >= 0; --q) {
       double acc = sr[q];
