@@ -273,9 +273,10 @@ def run_fnlh(args):
         fnlh.fnlh_relax(dm, J, p.omega, B, X, SWEEPS, fnlh.FNLH_F64, ws)
         fnlh.fnlh_residual(dm, J, p.omega, B, X, norms=norms, ws=ws)
 
-    # kernels launched per step: build, basis, pattern check (b = 6), block rotation; rotate B and X in; the sweeps;
-    # rotate out; residual + its reduction (the ncu launch list shows the same count)
-    launches_per_step = (4 if p.block == 6 else 3) + 2 + SWEEPS + 1 + 2
+    # kernels launched per step: build, basis, pattern check (b = 6), block rotation; rotate B and X in; the
+    # reciprocal-pivot table; the sweeps; rotate out; residual + its reduction (the ncu launch list shows the
+    # same count)
+    launches_per_step = (4 if p.block == 6 else 3) + 2 + 1 + SWEEPS + 1 + 2
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
