@@ -58,59 +58,56 @@ __device__ __forceinline__ void flux_jacobian(const double (&q)[BS], const doubl
   }
 }
 
-__device__ __forceinline__ void sound_and_un(const double* q, const double n[3], double gamma, double& a,
-                                             double& un, double& nn) {
-  const double ir = 1.0 / q[0];
-  const double u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
-  const double p = (gamma - 1.0) * (q[4] - 0.5 * q[0] * (u * u + v * v + w * w));
-  a = sqrt(gamma * p * ir);
-  un = u * n[0] + v * n[1] + w * n[2];
-  nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-}
-
-// |A|(Q, n) with the entropy fix f(l) = max(|l|, delta (|u_n| + a|n|)),
-// written through N = A - u_n I (rank two for the Euler block):
-//   |A| = f0 I + N^2 ((f+ + f-)/2 - f0) / c^2 + N (f+ - f-) / (2c),  c = a|n|,
-// which is the spectral form sum_k f(l_k) P_k with the projectors onto the
-// eigenspaces of u_n and u_n +- c.  Turbulence row: the scalar f(u_n).
+// |A|(Q, n) with the entropy fix f(l) = max(|l|, delta (|u_n| + a|n|)) on the
+// Euler block (the turbulence row gets the scalar f(u_n)); returns the
+// spectral radius |u_n| + a|n|.  On the Euler block N = A - u_n I has rank two:
+//   N = alpha p^T + beta q^T,  alpha = (1, v, H), beta = (0, n, u_n),
+//                              p = (-u_n, n, 0), q = (phi, -(gamma-1) v, gamma-1),
+// phi = (gamma-1)|v|^2/2, and the Gram products are p.alpha = q.beta = 0,
+// p.beta = |n|^2, q.alpha = (gamma-1)(H - |v|^2/2) = a^2.  The spectral form
+// |A| = sum_k f(l_k) P_k = f0 I + s2 N^2 + s1 N (projectors onto the
+// eigenspaces of u_n and u_n +- c, c = a|n|, s2 = ((f+ + f-)/2 - f0)/c^2,
+// s1 = (f+ - f-)/(2c)) therefore collapses to
+//   |A| = f0 I + [alpha beta] C [p q]^T,   C = [[s1, s2 |n|^2], [s2 a^2, s1]],
+// 70 multiply-adds instead of a 5x5 matrix product.
 template <int BS>
-__device__ __forceinline__ void abs_flux_jacobian(const double (&q)[BS], const double n[3], double gamma,
-                                                  double delta, double (&M)[BS][BS]) {
+__device__ __forceinline__ double abs_flux_jacobian(const double (&q)[BS], const double n[3], double gamma,
+                                                    double delta, double (&M)[BS][BS]) {
 #pragma unroll
   for (int r = 0; r < BS; ++r)
 #pragma unroll
     for (int c = 0; c < BS; ++c) M[r][c] = 0.0;
-  double a, un, nn;
-  sound_and_un(q, n, gamma, a, un, nn);
-  if (nn == 0.0) return;
-  double A[BS][BS];
-  flux_jacobian<BS>(q, n, gamma, A);
-  const double c = a * nn;
-  const double fix = delta * (fabs(un) + c);
+  const double g1 = gamma - 1.0;
+  const double ir = 1.0 / q[0];
+  const double v[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const double ke = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double pr = g1 * (q[4] - q[0] * ke);
+  const double a2 = gamma * pr * ir;
+  const double un = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const double nn2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  const double c = sqrt(a2) * sqrt(nn2);
+  const double lam = fabs(un) + c;
+  if (nn2 == 0.0) return lam;
+  const double fix = delta * lam;
   const double f0 = fmax(fabs(un), fix), fp = fmax(fabs(un + c), fix), fm = fmax(fabs(un - c), fix);
-  const double s2 = (0.5 * (fp + fm) - f0) / (c * c);
-  const double s1 = (fp - fm) / (2.0 * c);
-  double N[5][5];
+  const double ic = 1.0 / c;
+  const double s1 = 0.5 * (fp - fm) * ic;
+  const double s2 = (0.5 * (fp + fm) - f0) * ic * ic;
+  const double H = (q[4] + pr) * ir;
+  const double alpha[5] = {1.0, v[0], v[1], v[2], H};
+  const double beta[5] = {0.0, n[0], n[1], n[2], un};
+  const double pv[5] = {-un, n[0], n[1], n[2], 0.0};
+  const double qv[5] = {g1 * ke, -g1 * v[0], -g1 * v[1], -g1 * v[2], g1};
+  const double c01 = s2 * nn2, c10 = s2 * a2;
 #pragma unroll
-  for (int r = 0; r < 5; ++r)
+  for (int r = 0; r < 5; ++r) {
+    const double w0 = alpha[r] * s1 + beta[r] * c10;
+    const double w1 = alpha[r] * c01 + beta[r] * s1;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) N[r][k] = A[r][k] - (r == k ? un : 0.0);
-#pragma unroll
-  for (int r = 0; r < 5; ++r)
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      double n2 = 0.0;
-#pragma unroll
-      for (int t = 0; t < 5; ++t) n2 += N[r][t] * N[t][k];
-      M[r][k] = s2 * n2 + s1 * N[r][k] + (r == k ? f0 : 0.0);
-    }
+    for (int k = 0; k < 5; ++k) M[r][k] = w0 * pv[k] + w1 * qv[k] + (r == k ? f0 : 0.0);
+  }
   if (BS == 6) M[5][5] = f0;
-}
-
-__device__ __forceinline__ double spectral_radius(const double* q, const double n[3], double gamma) {
-  double a, un, nn;
-  sound_and_un(q, n, gamma, a, un, nn);
-  return fabs(un) + a * nn;
+  return lam;
 }
 
 struct BuildArgs {
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
       qb[m] = 0.5 * (qi[m] + qj[m]);
     }
     double M[BS][BS], Aj[BS][BS];
-    abs_flux_jacobian<BS>(qb, n, a.gamma, a.delta, M);
+    lsum += abs_flux_jacobian<BS>(qb, n, a.gamma, a.delta, M);
     flux_jacobian<BS>(qj, n, a.gamma, Aj);
     double* o = a.offd + (size_t)p * BS * BS;
 #pragma unroll
@@ -170,16 +167,14 @@ __global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
         o[r * BS + c] = 0.5 * (Aj[r][c] - M[r][c]);
         P[r][c] += 0.5 * M[r][c];
       }
-    lsum += spectral_radius(qb, n, a.gamma);
   }
   {
     double M[BS][BS];
-    abs_flux_jacobian<BS>(qi, nb, a.gamma, a.delta, M);
+    lsum += abs_flux_jacobian<BS>(qi, nb, a.gamma, a.delta, M);
 #pragma unroll
     for (int r = 0; r < BS; ++r)
 #pragma unroll
       for (int c = 0; c < BS; ++c) P[r][c] += 0.5 * M[r][c];
-    lsum += spectral_radius(qi, nb, a.gamma);
   }
   if (BS == 6) P[5][5] *= 2.0;
   const double scale = a.pseudo_time ? (1.0 + 1.0 / (a.eps * a.cfl)) : 1.0;
@@ -284,11 +279,30 @@ __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* 
     }
 }
 
+// b = 6: the basis Q = [e_5 | (Z5; 0)] that k_prepare_basis builds when the
+// mean-flow rows do not see the turbulence variable (exact zeros and one).
+template <int BS>
+__device__ __forceinline__ bool turbulence_first(const double* __restrict__ Q) {
+  if constexpr (BS != 6) {
+    return false;
+  } else {
+    bool st = Q[5 * 6] == 1.0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) st = st && Q[r * 6] == 0.0;
+#pragma unroll
+    for (int c = 1; c < 6; ++c) st = st && Q[5 * 6 + c] == 0.0;
+    return st;
+  }
+}
+
 // Rotated off-diagonal blocks Q_i^T J_ij Q_j, one thread per CSR entry (the
 // owning row found by binary search over row_ptr), written in every
-// requested precision (round to nearest).
+// requested precision (round to nearest).  Between two frozen-turbulence
+// bases the products skip the basis' structural zeros (300 instead of 432
+// multiply-adds; the same sums in the same order, so the same values).  Four
+// CTAs per SM (128 registers) beat three at 168 registers by 5% on GB300.
 template <int BS>
-__global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(128, 4) k_rotate_offd(int32_t n, int32_t nnz, const int32_t* __restrict__ row_ptr,
                                                      const int32_t* __restrict__ col_idx,
                                                      const double* __restrict__ offd, const double* __restrict__ rot,
                                                      double* __restrict__ o64, float* __restrict__ o32,
@@ -306,6 +320,41 @@ __global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, con
   const double* J = offd + (size_t)p * BS * BS;
   const double* Qj = rot + (size_t)j * BS * BS;
   const double* Qi = rot + (size_t)i * BS * BS;
+  auto emit = [&](int r, int c, double t) {
+    const size_t o = (size_t)p * BS * BS + r * BS + c;
+    if (o64) o64[o] = t;
+    if (o32) o32[o] = (float)t;
+    if (o16) o16[o] = __double2bfloat16(t);
+  };
+  if (turbulence_first<BS>(Qi) && turbulence_first<BS>(Qj)) {
+    // T = J Q_j: column 0 is J's last column; row 5 of Q_j is zero elsewhere
+#pragma unroll
+    for (int r = 0; r < BS; ++r) {
+      T[r][0] = J[r * BS + BS - 1];
+#pragma unroll
+      for (int c = 1; c < BS; ++c) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < BS - 1; ++k) t += J[r * BS + k] * Qj[k * BS + c];
+        T[r][c] = t;
+      }
+    }
+    // Q_i^T T: row 0 is T's last row; the rest skip row 5 of Q_i
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        double t = 0.0;
+        if (r == 0) {
+          t = T[BS - 1][c];
+        } else {
+#pragma unroll
+          for (int k = 0; k < BS - 1; ++k) t += Qi[k * BS + r] * T[k][c];
+        }
+        emit(r, c, t);
+      }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < BS; ++r)
 #pragma unroll
@@ -322,10 +371,7 @@ __global__ void __launch_bounds__(128) k_rotate_offd(int32_t n, int32_t nnz, con
       double t = 0.0;
 #pragma unroll
       for (int k = 0; k < BS; ++k) t += Qi[k * BS + r] * T[k][c];
-      const size_t o = (size_t)p * BS * BS + r * BS + c;
-      if (o64) o64[o] = t;
-      if (o32) o32[o] = (float)t;
-      if (o16) o16[o] = __double2bfloat16(t);
+      emit(r, c, t);
     }
 }
 
