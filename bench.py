@@ -347,7 +347,7 @@ def run_fnlh(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hex passage; see DESIGN.md)",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded perturbed hex passage, flow state and right-hand sides)",
             "config": workload_config(p), "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "final_rel_residual": [float(x) for x in rel],
