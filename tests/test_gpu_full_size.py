@@ -1,0 +1,121 @@
+"""GPU parity at the full sizes of the measured workloads, in the launch
+configurations the benchmark times, checked by the oracle.
+
+* 160x128x102 passage (2,088,960 nodes), b = 6, mean + 8 harmonics: the
+  FP32-block (30 inner sweeps per FP64 residual) and BF16-block (25 inner)
+  defect-correction solves reach a true FP64 residual of 1e-8 per system, and
+  the residual the library reports agrees with the oracle's.
+* Three blade rows (200,000 / 600,000 / 1,100,000 nodes, N = 2 / 8 / 4):
+  20 batched FP64 sweeps match the oracle's Jacobi per row to 1e-12; the
+  batched BF16 sweeps equal the per-row BF16 sweeps bit for bit; the
+  batched FP32 solve reaches 1e-8 on every row.
+* 256x200x156 passage (7,987,200 nodes), mean + 1 harmonic: the BF16 solve
+  reaches a true FP64 residual of 1e-8.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_01407_gb300 import fnlh, inputs
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+ZG = fnlh.FNLH_SOLVE_ZERO_GUESS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available()
+    fnlh.lib()
+
+
+@pytest.fixture(scope="module")
+def passage_c3():
+    p = inputs.config_problem("c3")
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16)
+    oj = _gpu.oracle_jacobian(p)
+    yield p, dm, J, B, oj
+    del dm, J, B
+    torch.cuda.empty_cache()
+
+
+def check_true_residual(oj, p, X, rel_gpu, tol=1e-8):
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+    assert np.all(true_rel <= 1.05 * tol), true_rel
+    # the library's FP64 residual is the oracle's up to rounding: the entries of r
+    # cancel terms of size ~|A||x| ~ ||B||, so the two agree to ~1e-13 of ||B||
+    assert np.allclose(rel_gpu, true_rel, rtol=1e-6, atol=1e-12), (rel_gpu, true_rel)
+
+
+@pytest.mark.parametrize("prec,inner", [(fnlh.FNLH_F32, 30), (fnlh.FNLH_BF16, 25)])
+def test_passage_mixed_solve_full_size(passage_c3, prec, inner):
+    p, dm, J, B, oj = passage_c3
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=prec)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, inner, 200, ws=ws, flags=ZG)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    check_true_residual(oj, p, X, rel)
+
+
+def blade_rows():
+    return [inputs.config_problem(key) for key in ("c4_row0", "c4_row1", "c4_row2")]
+
+
+def test_blade_rows_batched_full_size():
+    rows = blade_rows()
+    dev = [_gpu.device_problem(p) for p in rows]
+    # FP64 batched sweeps against the oracle, row by row
+    Xs = [torch.zeros_like(B) for _, _, B in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, (dm, J, B), X in zip(rows, dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F64), dtype=torch.uint8, device="cuda")
+    fnlh.fnlh_relax_batched(batch, 20, fnlh.FNLH_F64, ws=ws)
+    for p, X in zip(rows, Xs):
+        oj = _gpu.oracle_jacobian(p)
+        ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 20)
+        err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
+        assert np.all(err <= 1e-12), (p.name, err)
+        del oj, ref
+    # BF16, the benchmark's precision: batched equals per-row bit for bit
+    singles = []
+    for p, (dm, J, B) in zip(rows, dev):
+        X = torch.zeros_like(B)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, 20, fnlh.FNLH_BF16)
+        singles.append(X)
+    for X in Xs:
+        X.zero_()
+    fnlh.fnlh_relax_batched(batch, 20, fnlh.FNLH_BF16, ws=ws)
+    for X, ref in zip(Xs, singles):
+        assert torch.equal(X, ref)
+    # the mixed batched solve reaches 1e-8 on every row
+    for X in Xs:
+        X.zero_()
+    del ws
+    sws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32), dtype=torch.uint8, device="cuda")
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F32, 1e-8, 30, 200, ws=sws, flags=ZG)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    for p, X in zip(rows, Xs):
+        oj = _gpu.oracle_jacobian(p)
+        true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+        assert np.all(true_rel <= 1.05e-8), (p.name, true_rel)
+
+
+def test_large_passage_bf16_solve_full_size():
+    c = inputs.CONFIGS["c5"]
+    p = inputs.config_problem("c5", n_harm=1)
+    assert p.mesh.n_nodes == 7987200 and tuple(c["dims"]) == (256, 200, 156)
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_BF16)
+    X = torch.zeros_like(B)
+    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=fnlh.FNLH_BF16)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, 25, 200, ws=ws,
+                                              flags=ZG)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    x = X.cpu().numpy()
+    del dm, J, B, X, ws
+    torch.cuda.empty_cache()
+    oj = _gpu.oracle_jacobian(p)
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, x)
+    assert np.all(true_rel <= 1.05e-8), true_rel
+    assert np.allclose(rel, true_rel, rtol=1e-6, atol=1e-12), (rel, true_rel)
