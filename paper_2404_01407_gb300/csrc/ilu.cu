@@ -121,6 +121,7 @@ struct IluArgs {
   double* X;            // [n][C][b] iterate, caller layout
   int32_t* status;      // bit 1: a zero pivot
   int32_t masked;
+  int32_t last;         // forward pass over the top colour: y = z there, so it also updates x (FP64)
   uint64_t active[2];
   Systems sys;
 };
@@ -324,6 +325,9 @@ __device__ __forceinline__ void ilu_pivot_apply(const T* __restrict__ F, int K, 
 }
 
 // Forward pass over one colour: z_i = P_i^-1 (r_i - sum_{j earlier} A_ij z_j).
+// The top colour has no later neighbours, so its backward pass would only
+// copy y_i = z_i: in FP64 this pass adds it to x_i instead, and the
+// backward passes start one colour lower.
 template <int BS, typename T>
 __global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_constant__ IluArgs a) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,6 +371,16 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_consta
   for (int q = 0; q < BS; ++q) {
     e[2 * q] = yr[q];
     e[2 * q + 1] = yi[q];
+  }
+  if constexpr (sizeof(T) == 8) {  // FP32: x += Q e after the passes
+    if (a.last) {
+      double* xp = a.X + ((size_t)i * a.sys.C + ((k == 0) ? 0 : 2 * k - 1)) * BS;
+#pragma unroll
+      for (int q = 0; q < BS; ++q) {
+        xp[q] += yr[q];
+        if (k > 0) xp[BS + q] += yi[q];
+      }
+    }
   }
 }
 
@@ -574,11 +588,13 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
     for (int c = 0; c < ilu->n_colors; ++c) {
       a.begin = ilu->color_ptr[c];
       a.end = ilu->color_ptr[c + 1];
+      a.last = (c == ilu->n_colors - 1) ? 1 : 0;
       if (a.end <= a.begin) continue;
       k_ilu_forward<BS, T><<<grid_for((long long)(a.end - a.begin) * K, kIluThreads), kIluThreads, 0, s>>>(a);
       FNLH_LAUNCH_CHECK();
     }
-    for (int c = ilu->n_colors - 1; c >= 0; --c) {
+    a.last = 0;
+    for (int c = ilu->n_colors - 2; c >= 0; --c) {  // the top colour's y = z is final
       a.begin = ilu->color_ptr[c];
       a.end = ilu->color_ptr[c + 1];
       if (a.end <= a.begin) continue;
