@@ -398,6 +398,8 @@ def run_fnlh(args):
         torch.cuda.empty_cache()
         line["batched"] = batched_section(torch, fnlh, inputs, dev, args)
         torch.cuda.empty_cache()
+        line["batched_small_rows"] = batched_small_section(torch, fnlh, inputs, dev)
+        torch.cuda.empty_cache()
         line["rk_stages"] = rk_section(torch, fnlh, inputs, dev)
         torch.cuda.empty_cache()
         line["periodic"] = periodic_section(torch, fnlh, inputs, dev)
@@ -825,6 +827,71 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
             "batched_graph_ms": t_graph, "tuning": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm},
             "updates_per_s_graph": updates / (t_graph * 1e-3), "speedup_vs_per_row": t_rows / t_graph,
             "tuning_table": table}
+
+
+def batched_small_section(torch, fnlh, inputs, dev, sweeps=20):
+    """Rows the size of the paper's compressor (33k nodes) and turbine (72k nodes) meshes, where a sweep
+    takes microseconds: per-row launches against one batched launch per sweep, eager and captured in a
+    CUDA graph."""
+    specs = [("compressor-size row", (42, 28, 28), 4, 1.0, (1, 2, 3)),
+             ("turbine-size row", (60, 40, 30), 4, 1.6, (4, 5, 6))]
+    rows = []
+    for name, dims, N, ob, seeds in specs:
+        p = inputs.problem(dims, 6, N, 20.0, ob, seeds=seeds, name=name)
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+        J = fnlh.DeviceJacobian(dm, 6, fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16, dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+        B = torch.from_numpy(p.b).to(dev)
+        rows.append((p, dm, J, B, torch.zeros_like(B),
+                     fnlh.workspace(p.mesh.n_nodes, 6, N, dev, precision=fnlh.FNLH_F32)))
+    updates = sum(p.mesh.n_nodes * (1 + p.n_harm) for p, *_ in rows) * sweeps
+
+    def timeit(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def graphed(fn):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            fn()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    out = {"workload": "rows 42x28x28 (32,928 nodes) and 60x40x30 (72,000 nodes), b=6, mean + 4 harmonics, "
+                       f"{sweeps} sweeps"}
+    for pname in ("bf16", "f32"):
+        prec = fnlh.PRECISIONS[pname]
+
+        def per_row():
+            for p, dm, J, B, X, ws in rows:
+                fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec, ws)
+
+        batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
+        bws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device=dev)
+
+        def batched():
+            fnlh.fnlh_relax_batched(batch, sweeps, prec, ws=bws)
+
+        g_rows, g_batch = graphed(per_row), graphed(batched)
+        t = {"per_row_ms": timeit(per_row), "batched_ms": timeit(batched),
+             "per_row_graph_ms": timeit(g_rows.replay), "batched_graph_ms": timeit(g_batch.replay)}
+        t["updates_per_s_batched_graph"] = updates / (t["batched_graph_ms"] * 1e-3)
+        t["speedup_batched_graph_vs_per_row"] = t["per_row_ms"] / t["batched_graph_ms"]
+        out[pname] = t
+        del g_rows, g_batch, bws
+    return out
 
 
 def main():
