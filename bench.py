@@ -44,16 +44,17 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of the top kernel from the last ncu
 # capture of the kernel as it stands on this workload (profiles/k_sweep_f64_c2.md);
 # to be reset to None whenever the kernel changes
-NCU_TRAFFIC = {"k_sweep_f64_c2": 1269421000 + 177711616}
+NCU_TRAFFIC = {}  # refreshed from the next ncu capture of the changed kernel
 
 
 def tri_solve_flops(b: int, real: bool) -> int:
     """Flops of one shifted back-substitution (T + i s I) y = r with the per-node
-    real Schur factor T: 4 per off-diagonal term and 12 per diagonal division for a
-    complex system; 2 and 2 for the real (mean-flow) system."""
+    real Schur factor T and the pivot factors computed once per call: 4 per
+    off-diagonal term and 6 per row for the scaling by (d - i s) / (d^2 + s^2)
+    of a complex system; 2 and 1 for the real (mean-flow) system."""
     if real:
-        return b * (b - 1) + 2 * b
-    return 2 * b * (b - 1) + 12 * b
+        return b * (b - 1) + b
+    return 2 * b * (b - 1) + 6 * b
 
 
 def sweep_flops(n, nnz, b, n_harm, block_entries=None):

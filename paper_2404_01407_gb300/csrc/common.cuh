@@ -117,8 +117,10 @@ __device__ __forceinline__ void batch_recip(const double (&m)[BS], double (&inv)
 // (yr, yi) holds b on entry and y on return.  Cost O(BS^2) complex
 // operations instead of the O(BS^3) of a general block LU.  H may point to
 // global or shared memory (plain loads).
-// pivinv (nullable, FP64): the precomputed 1 / (d_k^2 + s^2) of this block and
-// shift, so that no division is left in the solve.
+// pivinv (nullable, FP64): per row k the precomputed pair
+// (d_k, s) / (d_k^2 + s^2) of this block and shift, so that
+// y_k = (a_r alpha_k + a_i beta_k) + i (a_i alpha_k - a_r beta_k) needs no
+// division and two fewer multiplies.
 template <int BS, typename T, typename TH>
 __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr)[BS], T (&yi)[BS],
                                            const T* __restrict__ pivinv = nullptr) {
@@ -127,13 +129,34 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
   bool tri = true;
 #pragma unroll
   for (int k = 0; k < BS - 1; ++k) tri = tri && (H[(k + 1) * BS + k] == TH(0));
+  if (tri && pivinv) {
+#pragma unroll
+    for (int k = BS - 1; k >= 0; --k) {
+      T ar = yr[k], ai = yi[k];
+#pragma unroll
+      for (int c = k + 1; c < BS; ++c) {
+        const T t = (T)H[k * BS + c];
+        ar -= t * yr[c];
+        ai -= t * yi[c];
+      }
+      T al, be;
+      if constexpr (sizeof(T) == 8) {  // the table is 16-byte aligned: one vector load per row
+        const double2 f = __ldg(reinterpret_cast<const double2*>(pivinv) + k);
+        al = f.x;
+        be = f.y;
+      } else {
+        al = pivinv[2 * k];
+        be = pivinv[2 * k + 1];
+      }
+      yr[k] = ar * al + ai * be;
+      yi[k] = ai * al - ar * be;
+    }
+    return;
+  }
   if (tri) {
     // 1 / (d_k^2 + s^2): in FP64 one division for the whole block
     T invs[BS];
-    if (pivinv) {
-#pragma unroll
-      for (int k = 0; k < BS; ++k) invs[k] = pivinv[k];
-    } else if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
       double m[BS];
 #pragma unroll
       for (int k = 0; k < BS; ++k) {
@@ -261,7 +284,7 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
 // [256, +partials)              residual partial sums  kResidualGrid x 2K doubles
 // norms                         final 2K doubles of the last residual
 // vec0, vec1, vec2              three [n][K][b] complex vectors (internal layout) in the precision's type
-// pivinv                        FP64 only: [n][K][b] reciprocal pivots of the shifted triangular solves
+// pivinv                        FP64 only: [n][K][b] pairs (d, s) / (d^2 + s^2) of the shifted triangular solves
 struct WsLayout {
   size_t status, partials, norms, vec[3], pivinv, total, vec_bytes;
 };
@@ -284,7 +307,7 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
   w.pivinv = (size_t)-1;
   if (precision == FNLH_F64) {
     w.pivinv = off;
-    off = align256(off + (size_t)n * K * block * sizeof(double));
+    off = align256(off + (size_t)n * K * block * 2 * sizeof(double));
   }
   w.total = off;
   return w;

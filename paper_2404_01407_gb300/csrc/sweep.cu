@@ -176,14 +176,15 @@ struct PivotArgs {
   int32_t K;
   const double* hess;
   const double* vol;
-  double* out;      // [n][K][b]
+  double* out;      // [n][K][b] pairs
   double omega[kMaxSys];
 };
 
-// Reciprocal pivots of every (node, system) triangular solve, once per call:
-// the sweeps then divide nowhere (an FP64 division is a multi-instruction
-// sequence on GB300's scarce FP64 units).  Mean flow: 1 / d_q; harmonic k:
-// 1 / (d_q^2 + (omega_k V_i)^2) with d_q the diagonal of the Schur factor.
+// Pivot factors of every (node, system) triangular solve, once per call: the
+// sweeps then divide nowhere (an FP64 division is a multi-instruction
+// sequence on GB300's scarce FP64 units).  Mean flow: (1 / d_q, 0); harmonic
+// k: (d_q, s) / (d_q^2 + s^2), s = omega_k V_i, d_q the diagonal of the
+// Schur factor, so that 1 / (d_q + i s) = alpha - i beta.
 template <int BS>
 __global__ void __launch_bounds__(256) k_pivot_inverses(const __grid_constant__ PivotArgs a) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,7 +195,16 @@ __global__ void __launch_bounds__(256) k_pivot_inverses(const __grid_constant__ 
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
     const double d = a.hess[(size_t)i * BS * BS + q * BS + q];
-    a.out[(size_t)g * BS + q] = (k == 0) ? 1.0 / d : 1.0 / (d * d + s * s);
+    double al, be;
+    if (k == 0) {
+      al = 1.0 / d;
+      be = 0.0;
+    } else {
+      const double inv = 1.0 / (d * d + s * s);
+      al = d * inv;
+      be = s * inv;
+    }
+    reinterpret_cast<double2*>(a.out)[(size_t)g * BS + q] = make_double2(al, be);
   }
 }
 

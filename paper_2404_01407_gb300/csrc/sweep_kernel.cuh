@@ -220,9 +220,10 @@ struct TileRow {
   const double* vol;
   const void* Bt;    // [n][K][b] complex, right-hand side in the rotated basis
   const int32_t* info;  // prep info word: 0 = the b = 6 frozen-turbulence pattern holds (FP64 skips its zeros)
-  // nullable, FP64: [n][K][b] reciprocal pivots (k = 0: 1 / d_q; k > 0: 1 / (d_q^2 + s_k^2)).
-  // Set only for the single-row kernel, whose mean flow takes the real path,
-  // so the complex solve reads it for k > 0 alone.
+  // nullable, FP64: [n][K][b] pairs of the triangular solves (k = 0: (1 / d_q, 0);
+  // k > 0: (d_q, s_k) / (d_q^2 + s_k^2)).  Set only for the single-row
+  // kernel, whose mean flow takes the real path, so the complex solve reads
+  // it for k > 0 alone.
   const double* pivinv;
 };
 
@@ -294,7 +295,7 @@ __device__ __forceinline__ void finish_pair(const TileRow& R, const SweepIO& io,
                                             Cvec<BS, T>& s) {
   const T shift = (T)(io.omega[k] * __ldg(R.vol + i));
   if constexpr (sizeof(T) == 8)
-    hess_solve<BS, T>(H, shift, s.re, s.im, R.pivinv ? R.pivinv + ((size_t)i * R.K + k) * BS : nullptr);
+    hess_solve<BS, T>(H, shift, s.re, s.im, R.pivinv ? R.pivinv + ((size_t)i * R.K + k) * BS * 2 : nullptr);
   else
     hess_solve<BS, T>(H, shift, s.re, s.im);
   store_slice<BS>((T*)io.Xout + ((size_t)i * R.K + k) * 2 * BS, s);
@@ -385,7 +386,7 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
     double inv[BS];
     if (R.pivinv) {
 #pragma unroll
-      for (int q = 0; q < BS; ++q) inv[q] = __ldg(R.pivinv + (size_t)i * R.K * BS + q);
+      for (int q = 0; q < BS; ++q) inv[q] = __ldg(R.pivinv + (size_t)i * R.K * BS * 2 + 2 * q);
     } else {
       double dg[BS];
 #pragma unroll
