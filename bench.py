@@ -564,7 +564,10 @@ def ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, reps=3):
     rp, ci = dm.row_ptr_host, dm.col_idx_host
     owner = np.repeat(np.arange(n), np.diff(rp))
     n_upper = int(np.unique(owner[color[ci] > color[owner]]).shape[0])
-    flops = K * (4 * b * b * nnz + 8 * b * b * (n + n_upper))
+    # gathers: 2 flops per structurally nonzero block entry and real column (the mean flow is one real
+    # column, a harmonic two); pivots: a dense complex P^-1 per harmonic, a real one for the mean flow
+    e = b * b - (b - 1) if fnlh.fnlh_prep_structured(J) else b * b
+    flops = 2 * e * nnz * C + (n + n_upper) * (8 * b * b * N + 2 * b * b)
     if prec == fnlh.FNLH_F64:  # original basis: FP64 blocks, r read and x updated in the caller's layout
         bytes_ = ((n + n_upper) * K * b * b * 2 * 8 + nnz * b * b * 8 + n * C * b * 8 + 4 * n * K * 2 * b * 8
                   + 2 * n * C * b * 8 + nnz * 4 + n * 8)

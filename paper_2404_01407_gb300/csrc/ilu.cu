@@ -109,6 +109,7 @@ struct IluArgs {
   const int32_t* row_ptr;
   const int32_t* cols;  // tagged column indices (col_of / side_of / cut_of)
   const double* offd;   // J_ij, original basis (FP64 smoother)
+  const int32_t* info;  // prep info word, nullable: 0 = the b = 6 frozen-turbulence pattern holds
   const double* diag;
   const double* D;
   const double* vol;
@@ -283,6 +284,26 @@ __device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int 
     xi[t] = yj[2 * t + 1];
   }
   if (side_of(cj)) phase_shift<BS, T>(xr, xi, side_of(cj), a.sys.phase[k]);
+  // FP64, b = 6 with frozen turbulence: rows 0..4 of the original-basis
+  // block skip their structurally zero column 5
+  bool pattern = false;
+  if constexpr (BS == 6 && sizeof(T) == 8) pattern = a.info != nullptr && __ldg(a.info) == 0;
+  if (pattern) {
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int t = 0; t < ((r < BS - 1) ? BS - 1 : BS); ++t) {
+        const T av = __ldg(a.offd + (size_t)p * BS * BS + r * BS + t);
+        if constexpr (kSubtract) {
+          sr[r] -= av * xr[t];
+          si[r] -= av * xi[t];
+        } else {
+          sr[r] += av * xr[t];
+          si[r] += av * xi[t];
+        }
+      }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < BS; ++r)
 #pragma unroll
@@ -454,6 +475,7 @@ static IluArgs ilu_args(const fnlh_mesh* m, const fnlh_jacobian* J, const fnlh_i
   a.row_ptr = m->row_ptr;
   a.cols = csr_columns(m, J);
   a.offd = J->offd;
+  a.info = prep_info(J);
   a.diag = J->diag;
   a.D = J->D;
   a.vol = m->vol;
