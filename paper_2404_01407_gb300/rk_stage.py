@@ -21,8 +21,6 @@ from __future__ import annotations
 
 from fractions import Fraction
 
-import numpy as np
-
 from . import fnlh
 
 # Table rk_coff
