@@ -17,7 +17,7 @@ from . import fnlh
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-SEARCH_THREADS = (128, 256)
+SEARCH_THREADS = (64, 128, 256)
 SEARCH_CTAS_PER_SM = (0, 2, 4, 8)  # 0: one CTA per tile
 
 

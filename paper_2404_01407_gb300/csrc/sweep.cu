@@ -9,7 +9,7 @@
 // Design (GB300): one thread per (node, system); the off-diagonal product is
 // accumulated in registers and the shifted diagonal system solved in
 // registers.  FP64: a CTA owns 32 nodes and each warp whole systems for them
-// (the mean flow's warp runs a real-only path).  FP32/BF16: 128-pair tiles
+// (the mean flow's warp runs a real-only path).  FP32/BF16: 64-pair tiles
 // whose blocks are staged in shared memory when a node serves enough systems.
 // The sweeps run in the per-node Hessenberg basis prepared by
 // fnlh_prepare (x = Q x~), where the diagonal block of system k is
@@ -29,7 +29,7 @@
 namespace fnlh {
 
 constexpr int kSweepThreads = 256;      // FP64 sweep CTA (32 nodes x up to 8 system warps)
-constexpr int kSweepThreadsF32 = 128;   // FP32 sweep tile: 128 (node, system) pairs
+constexpr int kSweepThreadsF32 = 64;    // FP32 sweep tile: 64 (node, system) pairs
 
 struct SweepArgs {
   TileRow row;
@@ -59,10 +59,11 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_f64(const __grid_con
 }
 
 // FP32 arithmetic on FP32 or BF16 blocks, staged per CTA tile.  64 registers:
-// eight 128-thread CTAs per SM (measured against 256-thread tiles at three or
-// four CTAs per SM: 15% faster on the 2.1M-node, 9-system workload).
+// sixteen 64-thread CTAs per SM (measured on GB300: 0.5-1.3% faster than eight
+// 128-thread CTAs, and those 15% faster than 256-thread tiles at three or four
+// CTAs per SM on the 2.1M-node, 9-system workload).
 template <int BS, typename TJ>
-__global__ void __launch_bounds__(kSweepThreadsF32, 8) k_sweep_f32(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreadsF32, 16) k_sweep_f32(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(16) float smem[];
   const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr, a.phase};
   sweep_tile_f32<BS, TJ>(a.row, io, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
@@ -620,7 +621,7 @@ __device__ __forceinline__ void batched_tile(const BatchArgs& a, long long t, fl
 }
 
 // One CTA per tile.  FP32: 64 registers (up to 256 threads, four CTAs per SM;
-// 128 threads, eight); FP64 thread-per-pair needs 128.
+// 64 threads, sixteen); FP64 thread-per-pair needs 128.
 template <int BS, typename TJ, typename T>
 __global__ void __launch_bounds__(kSweepThreads, (sizeof(T) == 8) ? 2 : 4)
     k_sweep_batched(const __grid_constant__ BatchArgs a) {

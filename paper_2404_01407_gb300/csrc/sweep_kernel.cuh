@@ -416,7 +416,7 @@ __device__ __forceinline__ void sweep_node_f64(const TileRow& R, const SweepIO& 
 
 // s -= J x for one staged FP32 block, consumed row by row from shared
 // memory: six live block entries instead of thirty-six keep the register
-// count (64, eight CTAs per SM) without spilling.
+// count (64, sixteen 64-thread CTAs per SM) without spilling.
 template <int BS>
 __device__ __forceinline__ void spmv_rows_smem(const float* jb, const Cvec<BS, float>& x, Cvec<BS, float>& s) {
 #pragma unroll
