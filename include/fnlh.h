@@ -262,7 +262,9 @@ int fnlh_solve(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm, co
 /* Batched form: `sweeps` sweeps of fnlh_relax on several blade rows of
  * different sizes and harmonic counts (the multi-row FNLH setting of the
  * paper's Results) with one kernel launch per sweep over a tile list
- * spanning every row (one CTA per tile, or a persistent grid).  At most 8
+ * spanning every row (one CTA per tile, or a persistent grid) -- two when
+ * FP32/BF16 rows that stage their blocks in shared memory (K >= 6 systems)
+ * are mixed with rows that do not.  At most 8
  * rows, all with the same block size.  tuning may be NULL (defaults).  workspace: at
  * least the sum of fnlh_workspace_bytes of the rows plus
  * fnlh_batched_extra_bytes(n_rows).  Asynchronous, graph-capturable. */

@@ -572,7 +572,8 @@ int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const dou
 // ----------------------------------------------------------- batched rows
 //
 // Several blade rows (different meshes and harmonic counts) in one launch per
-// sweep.  The (node, system) pairs of every row are cut into tiles of
+// sweep (two when rows that stage their blocks are mixed with rows that do
+// not).  The (node, system) pairs of every row are cut into tiles of
 // blockDim.x consecutive pairs; the grid walks the global tile list -- one
 // CTA per tile, or a persistent grid of SMs x ctas_per_sm CTAs striding over
 // it -- so the rows share one launch and one tail instead of each paying its
@@ -595,16 +596,17 @@ struct BatchRow {
 
 struct BatchArgs {
   int32_t n_rows, parity, smem_floats, x_zero;  // x_zero: the iterate is zero (first sweep of a correction)
-  long long n_tiles;
+  long long tile_base, tile_end;  // the tiles [tile_base, tile_end) of this launch
+  int32_t order[kMaxBatchRows];   // row indices in tile order (rows that stage their blocks first)
   BatchRow row[kMaxBatchRows];
 };
 
 // One tile t of the global tile list.
 template <int BS, typename TJ, typename T>
 __device__ __forceinline__ void batched_tile(const BatchArgs& a, long long t, float* smem) {
-  int r = 0;
-  while (r + 1 < a.n_rows && t >= a.row[r + 1].tile0) ++r;
-  const BatchRow& D = a.row[r];
+  int q = 0;
+  while (q + 1 < a.n_rows && t >= a.row[a.order[q + 1]].tile0) ++q;
+  const BatchRow& D = a.row[a.order[q]];
   const SweepIO io{D.x[a.parity], D.x[a.parity ^ 1], D.omega, D.masked ? D.active : nullptr, D.phase};
   const long long g0 = (t - D.tile0) * blockDim.x;
   if constexpr (sizeof(T) == 8) {
@@ -626,7 +628,7 @@ template <int BS, typename TJ, typename T>
 __global__ void __launch_bounds__(kSweepThreads, (sizeof(T) == 8) ? 2 : 4)
     k_sweep_batched(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) float smem[];
-  batched_tile<BS, TJ, T>(a, blockIdx.x, smem);
+  batched_tile<BS, TJ, T>(a, a.tile_base + blockIdx.x, smem);
 }
 
 // Persistent form: a grid of SMs x ctas_per_sm CTAs striding over the tile
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(kSweepThreads, (sizeof(T) == 8) ? 2 : 4)
 template <int BS, typename TJ, typename T>
 __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_batched_persistent(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) float smem[];
-  for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) batched_tile<BS, TJ, T>(a, t, smem);
+  for (long long t = a.tile_base + blockIdx.x; t < a.tile_end; t += gridDim.x) batched_tile<BS, TJ, T>(a, t, smem);
 }
 
 size_t batched_extra_bytes(int n_rows) { return n_rows > 0 ? 256 : 0; }
@@ -643,9 +645,10 @@ size_t batched_extra_bytes(int n_rows) { return n_rows > 0 ? 256 : 0; }
 // Launch shape, operands and workspace slices of a batch.
 struct BatchPlan {
   int threads;
-  unsigned grid;
   bool persistent;
-  size_t smem;
+  size_t smem;            // dynamic shared memory of the staged group's launches
+  long long split, n_tiles;  // tiles [0, split) belong to rows that stage their blocks, [split, n_tiles) do not
+  unsigned grid[2];       // grid of the staged group's and of the other group's launch
   SweepOperands ops[kMaxBatchRows];
   Systems sys[kMaxBatchRows];
   char* base[kMaxBatchRows];  // the row's workspace slice (ws_layout of its size and precision)
@@ -690,16 +693,31 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
     D.row.pivinv = nullptr;  // the batched FP64 tile divides in place
     D.x[0] = base + W.vec[1];
     D.x[1] = base + W.vec[2];
-    D.tile0 = tiles;
     D.active[0] = D.active[1] = ~0ull;
-    tiles += ((long long)D.row.n * D.row.K + P.threads - 1) / P.threads;
-    if (D.row.stage) kmin = std::min(kmin, sys.K);
+    if (sizeof(T) == 4 && D.row.stage) kmin = std::min(kmin, sys.K);
     for (int k = 0; k < kMaxSys; ++k) {
       D.omega[k] = sys.omega[k];
       D.phase[k] = sys.phase[k];
     }
   }
-  a.n_tiles = tiles;
+  // Tiles in two groups: the rows that stage their blocks in shared memory
+  // (FP32 with K >= kStageMinSystems), then the rest.  Each group gets its
+  // own launch per sweep, so that the rows that read their blocks through L1
+  // do not run on SMs configured for the staged rows' shared memory (mixing
+  // them in one launch cost 3% on three rows with K = 3, 9, 5).
+  int q = 0;
+  P.split = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int r = 0; r < n_rows; ++r) {
+      BatchRow& D = a.row[r];
+      const bool staged = sizeof(T) == 4 && D.row.stage;
+      if (staged != (pass == 0)) continue;
+      a.order[q++] = r;
+      D.tile0 = tiles;
+      tiles += ((long long)D.row.n * D.row.K + P.threads - 1) / P.threads;
+      if (pass == 0) P.split = tiles;
+    }
+  P.n_tiles = tiles;
   P.smem = 0;
   P.persistent = ctas_per_sm > 0;
   if constexpr (sizeof(T) == 4) {
@@ -712,8 +730,11 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
       if (rc) return rc;
     }
   }
-  const long long grid_ll = P.persistent ? std::min<long long>(tiles, (long long)sms * ctas_per_sm) : tiles;
-  P.grid = (unsigned)std::max<long long>(grid_ll, 1);
+  const long long group[2] = {P.split, P.n_tiles - P.split};
+  for (int g = 0; g < 2; ++g) {
+    const long long grid_ll = P.persistent ? std::min<long long>(group[g], (long long)sms * ctas_per_sm) : group[g];
+    P.grid[g] = (unsigned)std::max<long long>(grid_ll, 1);
+  }
   return FNLH_OK;
 }
 
@@ -725,9 +746,13 @@ int batch_launch(BatchArgs& a, const BatchPlan& P, int sweeps, int x_zero, cudaS
   if (rc) return rc;
   for (int it = 0; it < sweeps; ++it) {
     a.x_zero = (it == 0) ? x_zero : 0;
-    if (a.n_tiles > 0) {
-      if (P.persistent) k_sweep_batched_persistent<BS, TJ, T><<<P.grid, P.threads, P.smem, s>>>(a);
-      else k_sweep_batched<BS, TJ, T><<<P.grid, P.threads, P.smem, s>>>(a);
+    for (int g = 0; g < 2; ++g) {  // the staged rows' tiles, then the others'
+      a.tile_base = g ? P.split : 0;
+      a.tile_end = g ? P.n_tiles : P.split;
+      if (a.tile_end <= a.tile_base) continue;
+      const size_t smem = g ? 0 : P.smem;
+      if (P.persistent) k_sweep_batched_persistent<BS, TJ, T><<<P.grid[g], P.threads, smem, s>>>(a);
+      else k_sweep_batched<BS, TJ, T><<<P.grid[g], P.threads, smem, s>>>(a);
       FNLH_LAUNCH_CHECK();
     }
     a.parity ^= 1;
