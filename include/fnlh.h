@@ -64,7 +64,7 @@ enum fnlh_status {
     FNLH_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
     FNLH_ERR_NONFINITE = -3,     /* a residual norm is NaN or Inf */
     FNLH_ERR_DIVERGED = -4,      /* residual grew by more than 1e3 over its start */
-    FNLH_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+    FNLH_ERR_TIMEOUT = -5,       /* reserved: a bounded device wait gave up (no kernel here waits) */
     FNLH_ERR_UNSUPPORTED = -6,   /* block size not 5 or 6, too many harmonics */
     FNLH_ERR_WORKSPACE = -7,     /* workspace or prep blob too small / missing */
     FNLH_ERR_NOT_CONVERGED = -8, /* iteration limit reached above tolerance */

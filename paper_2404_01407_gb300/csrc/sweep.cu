@@ -37,7 +37,6 @@ struct SweepArgs {
   void* Xout;
   int32_t x_zero;
   int32_t smem_floats;
-  int32_t* status;  // workspace status word (bit 0: a bounded wait timed out)
   int32_t masked;   // 0: every system is swept; 1: only the systems set in `active`
   uint64_t active[2];
   double omega[kMaxSys];
@@ -345,7 +344,7 @@ int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
 // (or from zero when x_zero), returns the buffer holding the result.
 template <int BS, typename TJ, typename T>
 int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, const T* Bt, T* x0, T* x1,
-               int sweeps, int x_zero, int32_t* status, cudaStream_t s, T** result,
+               int sweeps, int x_zero, cudaStream_t s, T** result,
                const uint64_t* active = nullptr, const double* pivinv = nullptr) {
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -361,7 +360,6 @@ int run_sweeps(const fnlh_mesh* m, const SweepOperands& op, const Systems& sys, 
   a.row.Bt = Bt;
   a.row.info = op.info;
   a.row.pivinv = pivinv;
-  a.status = status;
   a.masked = active ? 1 : 0;
   a.active[0] = active ? active[0] : ~0ull;
   a.active[1] = active ? active[1] : ~0ull;
@@ -411,7 +409,7 @@ int relax_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     pivinv = at<double>(ws, W.pivinv);
     if ((rc = pivot_inverses<BS>(m, (const double*)op.hess, sys, pivinv, s))) return rc;
   }
-  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, at<int32_t>(ws, W.status), s, &res, nullptr,
+  if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, bt, x0, x1, sweeps, 0, s, &res, nullptr,
                                   pivinv)))
     return rc;
   return rotate_out<BS, T>(n, sys.K, op.rot, res, X, 0, s);
@@ -470,7 +468,6 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   const WsLayout W = ws_layout(J->n_nodes, BS, n_harm, precision);
   const int n = J->n_nodes, K = sys.K;
   double* norms = at<double>(ws, W.norms);
-  int32_t* status = at<int32_t>(ws, W.status);
   T* v0 = at<T>(ws, W.vec[0]);
   T* v1 = at<T>(ws, W.vec[1]);
   T* v2 = at<T>(ws, W.vec[2]);
@@ -498,21 +495,14 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     pivinv = at<double>(ws, W.pivinv);
     if ((rc = pivot_inverses<BS>(m, (const double*)op.hess, sys, pivinv, s))) return rc;
   }
-  FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   for (;;) {
     // mixed: Q^T r in FP32 straight into v0; FP64 defect correction: r into v2
     double* r64 = (defect && !mixed) ? (double*)v2 : nullptr;
     rc = residual_launch(m, J, sys, B, X, r64, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms, ws, s);
     x_zero = false;
     if (rc) return rc;
-    int32_t hstatus = 0;
     FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
-    FNLH_CUDA_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FNLH_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hstatus) {
-      rc = FNLH_ERR_TIMEOUT;
-      break;
-    }
     rc = check_norms(hn, K, tol, &ck, checks == 0, &conv);
     ++checks;
     if (rc || conv || checks >= max_checks) break;
@@ -526,7 +516,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       if constexpr (sizeof(T) == 8) {
         if ((rc = rotate_in<BS, T>(n, K, op.rot, (const double*)v2, v0, s))) return rc;
       }
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, status, s, &res, act, pivinv))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, v1, v2, inner, 1, s, &res, act, pivinv))) return rc;
       const long long count = (long long)n * K;
       if constexpr (sizeof(T) == 4) {
         if (count > 0) {
@@ -538,7 +528,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       }
     } else {
       T* other = (cur == v1) ? v2 : v1;
-      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, status, s, &res, act, pivinv))) return rc;
+      if ((rc = run_sweeps<BS, TJ, T>(m, op, sys, v0, cur, other, inner, 0, s, &res, act, pivinv))) return rc;
       cur = res;
       if ((rc = rotate_out<BS, T>(n, K, op.rot, res, X, 0, s))) return rc;
     }
@@ -799,7 +789,6 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
   const bool mixed = sizeof(T) == 4;
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
-  int32_t* status = at<int32_t>(P.base[0], 0);
   for (int r = 0; r < n_rows; ++r) {
     const BatchRow& D = a.row[r];
     if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(rows[r].X, 0, sizeof(double) * (size_t)D.row.n * P.sys[r].C * BS, s));
@@ -808,7 +797,6 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
       if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].X, (T*)D.x[0], s))) return rc;
     }
   }
-  FNLH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   a.parity = 0;
   std::vector<double> hn(2 * kMaxSys * n_rows);
   std::vector<double> rel(kMaxSys * n_rows, 0.0);
@@ -827,13 +815,7 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
                                     cudaMemcpyDeviceToHost, s));
     }
     x_zero = false;
-    int32_t hstatus = 0;
-    FNLH_CUDA_TRY(cudaMemcpyAsync(&hstatus, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FNLH_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hstatus) {
-      rc = FNLH_ERR_TIMEOUT;
-      break;
-    }
     double worst = 0.0;
     bool finite = true;
     for (int r = 0; r < n_rows; ++r)
