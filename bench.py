@@ -159,7 +159,7 @@ def max_over_ranks(x, world, device="cuda"):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(p, budget_s=15.0, max_sweeps=30):
+def cpu_oracle_rate(p, budget_s=15.0, max_sweeps=100):
     """The oracle as it stands on the host cores: one build, S sweeps, one residual."""
     import oracle
 
