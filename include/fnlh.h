@@ -298,8 +298,10 @@ int fnlh_solve_batched(const fnlh_row *rows, int32_t n_rows, int32_t precision, 
  * whose memory pool owns the whole device budget, or a caller inside a CUDA
  * stream capture, where cudaMalloc is not allowed -- and therefore cannot
  * provide the workspace fnlh_residual needs.  The call allocates nothing.
- * Its first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * Every call looks up the array's address in the current context (a lookup
+ * that allocates nothing); the first call on a device may also load the
+ * library's device code there, so make that first call before any stream
+ * capture.  All
  * calls share the one array: calls that may run at the same time on the GPU
  * (other streams or host threads) race on it and must be serialised by the
  * caller.  A problem too large for the array (impossible for

@@ -1,8 +1,8 @@
 // Jacobian assembly and sweep preparation (FP64).
 //
-// Paper: arXiv 2404.01407, Eq. precon (implicit K = P/(eps sigma) + J with
-// J = dR/dQ "assembled using the information of the immediate neighbours with
-// first-order spatial accuracy") and "Solution Update" (J assembled once per
+// Paper: arXiv 2404.01407, Eq. precon (implicit K = P/(eps sigma) + J, where
+// J = dR/dQ is an approximate, first-order Jacobian built from each node's
+// immediate neighbours only) and "Solution Update" (J assembled once per
 // nonlinear iteration and shared by the mean flow and every harmonic).
 //
 // Both kernels here run once per nonlinear iteration, off the sweep loop.

@@ -1,8 +1,8 @@
 // FP64 linear residual r_k = B_k - A_k x_k and its per-system 2-norms.
 //
-// Paper: arXiv 2404.01407, Results ("A fixed threshold of 0.01 is used for the
-// linear residual"): the stopping rule compares ||B - A x||_2 with its
-// initial value, for the mean flow and each harmonic.  Here the residual is
+// Paper: arXiv 2404.01407, Results, Table fnlh_para (linear-residual
+// threshold): each linear solve stops once ||B - A x||_2 has dropped by a
+// fixed factor from its initial value, for the mean flow and each harmonic.  Here the residual is
 // always formed in FP64 from the FP64 blocks in the original basis, which is
 // what lets the mixed-precision sweeps be corrected back to FP64 accuracy.
 //
@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -291,25 +290,16 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
 constexpr size_t kNoAllocScratchDoubles = (size_t)kResidualGrid * 2 * kMaxSys;
 static __device__ __align__(256) double g_residual_scratch[kNoAllocScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_scratch_mu;
-static double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  The name
-// g_residual_scratch in host code is only a host-side handle, so the address
-// is looked up once per device with that device current and cached.
+// Device address of the scratch array in the current context.  The name
+// g_residual_scratch in host code is only a host-side handle; the address is
+// looked up on every call (the lookup allocates nothing), so that a context
+// created after a device reset, or another context made current on the same
+// device, never receives an address from an earlier one.
 static int scratch_address(double** out) {
-  int dev = 0;
-  FNLH_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return FNLH_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    double* p = nullptr;
-    FNLH_CUDA_TRY(cudaGetSymbolAddress((void**)&p, g_residual_scratch));
-    if (!p) return FNLH_ERR_CUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  double* p = nullptr;
+  FNLH_CUDA_TRY(cudaGetSymbolAddress((void**)&p, g_residual_scratch));
+  if (!p) return FNLH_ERR_CUDA;
+  *out = p;
   return FNLH_OK;
 }
 

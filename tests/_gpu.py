@@ -40,3 +40,26 @@ def rel_err_per_system(x, ref, n_harm):
         d = np.linalg.norm(x[:, c, :] - ref[:, c, :])
         out.append(d / max(np.linalg.norm(ref[:, c, :]), 1e-300))
     return np.array(out)
+
+
+def max_err_per_system(x, ref, n_harm):
+    """max_i |x_k,i - ref_k,i| / max_i |ref_k,i| per system (mean first), over
+    every real and imaginary entry of the system."""
+    out = []
+    cols = [[0]] + [[2 * k - 1, 2 * k] for k in range(1, n_harm + 1)]
+    for c in cols:
+        d = np.abs(x[:, c, :] - ref[:, c, :]).max(initial=0.0)
+        out.append(d / max(np.abs(ref[:, c, :]).max(initial=0.0), 1e-300))
+    return np.array(out)
+
+
+def assert_fp64_parity(x, ref, n_harm, tol=1e-12):
+    """The FP64 parity bar, per system: the 2-norm of the difference within
+    tol of the reference's 2-norm AND every single entry within tol of the
+    reference's largest entry (a 2-norm alone lets one wrong entry of a large
+    system hide below the bar)."""
+    err2 = rel_err_per_system(x, ref, n_harm)
+    errinf = max_err_per_system(x, ref, n_harm)
+    assert np.all(err2 <= tol), ("2-norm", err2)
+    assert np.all(errinf <= tol), ("max-entry", errinf)
+    return err2, errinf

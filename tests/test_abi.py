@@ -217,3 +217,21 @@ def test_ilu_sizes_and_validation():
     gap = fnlh.fnlh_ilu(2, vol, vol, short, ctypes.c_void_p(4096), 1 << 20, fnlh.FNLH_F64, 0, 0)
     assert L.fnlh_ilu_factor(ctypes.byref(m), ctypes.byref(J5), 1, om, ctypes.byref(gap), vol, 1 << 20,
                              None) == fnlh.FNLH_ERR_ARG
+
+
+def test_probe_library_exports_every_declared_symbol():
+    """The peak probe beside the library (include/fnlh_probe.h) builds and
+    exports its declared symbols; argument checks need no GPU."""
+    from paper_2404_01407_gb300 import peaks
+
+    text = open(os.path.join(ROOT, "include", "fnlh_probe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    declared = sorted(set(re.findall(r"\b(fnlh_\w+)\s*\(", text)))
+    assert declared == ["fnlh_probe_chains", "fnlh_probe_fma", "fnlh_probe_threads_per_block"]
+    lib = peaks.probe_lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert lib.fnlh_probe_threads_per_block() == 256 and lib.fnlh_probe_chains() == 8
+    ms = ctypes.c_float(0.0)
+    assert lib.fnlh_probe_fma(2, 1, 1, None, ctypes.byref(ms), None) == -1  # bad precision: rejected on the host
+    assert lib.fnlh_probe_fma(0, 0, 1, None, ctypes.byref(ms), None) == -1

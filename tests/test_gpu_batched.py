@@ -60,8 +60,7 @@ def test_batched_solve_equals_per_row_solves(prec):
     assert rel.shape == (3 + 9 + 5,)
     for X, ref, (p, *_r) in zip(Xs, singles, dev):
         if prec == fnlh.FNLH_F64:
-            err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-            assert np.all(err <= 1e-13), err
+            _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm, tol=1e-13)
         else:
             assert np.array_equal(X.cpu().numpy(), ref)
 
@@ -79,7 +78,7 @@ def test_batched_mixed_solve_reaches_1e8(prec):
     for X, p in zip(Xs, probs):
         oj = _gpu.oracle_jacobian(p)
         true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-        assert np.all(true_rel <= 1.05e-8), true_rel
+        assert np.all(true_rel <= 1e-8), true_rel
 
 
 def test_batched_solve_with_partitioned_and_periodic_rows():
@@ -96,8 +95,62 @@ def test_batched_solve_with_partitioned_and_periodic_rows():
         m = p.mesh
         oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl, periodic=m.periodic)
         true_rel = oracle.rel_residuals(oj, m.vol, p.omega, p.b, X.cpu().numpy(), sigma=p.phase)
-        assert np.all(true_rel <= 1.05e-8), true_rel
+        assert np.all(true_rel <= 1e-8), true_rel
     ws64 = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
     with pytest.raises(fnlh.FnlhError) as e:
         fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F64, 1e-8, 10, 60, ws=ws64)
     assert e.value.status == fnlh.FNLH_ERR_UNSUPPORTED
+
+
+def _capture(fn):
+    """Capture fn() in a CUDA graph on a side stream (one warm-up call first)."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        fn(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    return g
+
+
+@pytest.mark.parametrize("tuning", [None, (64, 0), (128, 2)])
+def test_batched_relax_graph_replay_matches_oracle(tuning):
+    """The benchmark's timed form of the batched launch: fnlh_relax_batched
+    captured once in a CUDA graph and replayed.  FP64 replays match the
+    oracle's Jacobi row by row (every entry within 1e-12 of the system's
+    largest); BF16 replays equal the direct call bit for bit and stay within
+    the low-precision bound of the oracle; two replays give identical bits."""
+    sweeps = 15
+    probs = rows_problem()
+    dev = device_rows(probs)
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    tn = None if tuning is None else fnlh.fnlh_tuning(*tuning)
+    refs = [oracle.jacobi(_gpu.oracle_jacobian(p), p.mesh.vol, p.omega, p.b, sweeps) for p in probs]
+    for prec in (fnlh.FNLH_F64, fnlh.FNLH_BF16):
+        ws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+        for X in Xs:
+            X.zero_()
+        fnlh.fnlh_relax_batched(batch, sweeps, prec, tuning=tn, ws=ws)
+        direct = [X.clone() for X in Xs]
+        g = _capture(lambda s: fnlh.fnlh_relax_batched(batch, sweeps, prec, tuning=tn, ws=ws, stream=s))
+        replays = []
+        for _ in range(2):
+            for X in Xs:
+                X.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            replays.append([X.clone() for X in Xs])
+        for X1, X2, Xd, ref, p in zip(replays[0], replays[1], direct, refs, probs):
+            assert torch.equal(X1, X2)
+            assert torch.equal(X1, Xd)
+            if prec == fnlh.FNLH_F64:
+                _gpu.assert_fp64_parity(X1.cpu().numpy(), ref, p.n_harm)
+            else:
+                err = _gpu.rel_err_per_system(X1.cpu().numpy(), ref, p.n_harm)
+                assert np.all(err <= 5e-2), err
+        del g, ws

@@ -44,7 +44,7 @@ def passage_c3():
 
 def check_true_residual(oj, p, X, rel_gpu, tol=1e-8):
     true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-    assert np.all(true_rel <= 1.05 * tol), true_rel
+    assert np.all(true_rel <= tol), true_rel
     # the library's FP64 residual is the oracle's up to rounding: the entries of r
     # cancel terms of size ~|A||x| ~ ||B||, so the two agree to ~1e-13 of ||B||
     assert np.allclose(rel_gpu, true_rel, rtol=1e-6, atol=1e-12), (rel_gpu, true_rel)
@@ -75,8 +75,7 @@ def test_blade_rows_batched_full_size():
     for p, X in zip(rows, Xs):
         oj = _gpu.oracle_jacobian(p)
         ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 20)
-        err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-        assert np.all(err <= 1e-12), (p.name, err)
+        _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
         del oj, ref
     # BF16, the benchmark's precision: batched equals per-row bit for bit
     singles = []
@@ -99,7 +98,7 @@ def test_blade_rows_batched_full_size():
     for p, X in zip(rows, Xs):
         oj = _gpu.oracle_jacobian(p)
         true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-        assert np.all(true_rel <= 1.05e-8), (p.name, true_rel)
+        assert np.all(true_rel <= 1e-8), (p.name, true_rel)
 
 
 def test_large_passage_bf16_solve_full_size():
@@ -117,5 +116,30 @@ def test_large_passage_bf16_solve_full_size():
     torch.cuda.empty_cache()
     oj = _gpu.oracle_jacobian(p)
     true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, x)
-    assert np.all(true_rel <= 1.05e-8), true_rel
+    assert np.all(true_rel <= 1e-8), true_rel
+    assert np.allclose(rel, true_rel, rtol=1e-6, atol=1e-12), (rel, true_rel)
+
+
+def test_large_passage_bf16_solve_n16_full_size():
+    """The large case exactly as the benchmark times it: 256x200x156 (7,987,200
+    nodes), mean + 16 harmonics, BF16 blocks, 25 inner sweeps per FP64
+    residual, from zero to 1e-8.  The oracle's residual on the returned x
+    (about 40 GB of host arrays: its FP64 Jacobian, B and x) certifies every
+    one of the 17 systems at 1e-8 and agrees with the residual the library
+    reports."""
+    p = inputs.config_problem("c5")
+    assert p.mesh.n_nodes == 7987200 and p.n_harm == 16
+    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_BF16)
+    X = torch.empty_like(B)
+    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=fnlh.FNLH_BF16)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, 25, 200, ws=ws,
+                                              flags=ZG)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    x = X.cpu().numpy()
+    del dm, J, B, X, ws
+    torch.cuda.empty_cache()
+    oj = _gpu.oracle_jacobian(p)
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, x)
+    assert true_rel.shape == (17,)
+    assert np.all(true_rel <= 1e-8), true_rel
     assert np.allclose(rel, true_rel, rtol=1e-6, atol=1e-12), (rel, true_rel)

@@ -57,8 +57,7 @@ def test_ilu_iterations_match_oracle(dims, block, N, greedy):
     X = torch.from_numpy(x0.copy()).cuda()
     run_iterations(dm, J, ilu, p, B, X, 6)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 6, ilu.color_host, X0=x0)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_ilu_periodic_passage_matches_oracle():
@@ -67,8 +66,7 @@ def test_ilu_periodic_passage_matches_oracle():
     X = torch.zeros_like(B)
     run_iterations(dm, J, ilu, p, B, X, 5)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 5, ilu.color_host, sigma=p.phase)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_ilu_odd_pitch_greedy_colouring_matches_oracle():
@@ -79,8 +77,7 @@ def test_ilu_odd_pitch_greedy_colouring_matches_oracle():
     X = torch.zeros_like(B)
     run_iterations(dm, J, ilu, p, B, X, 4)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 4, ilu.color_host, sigma=p.phase)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_ilu_partitioned_matches_oracle():
@@ -91,8 +88,7 @@ def test_ilu_partitioned_matches_oracle():
     X = torch.zeros_like(B)
     run_iterations(dm, J, ilu, p, B, X, 5)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 5, ilu.color_host, part=part)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 @pytest.mark.parametrize("precision", [fnlh.FNLH_F64, fnlh.FNLH_F32])
@@ -103,7 +99,7 @@ def test_ilu_solve_reaches_1e8(precision):
     st, its, rel = fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, 1e-8, 100, flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-    assert np.all(true_rel <= 1.05e-8), true_rel
+    assert np.all(true_rel <= 1e-8), true_rel
 
 
 def test_ilu_f32_iterations_bounded():
@@ -173,5 +169,4 @@ def test_ilu_larger_passage_matches_oracle():
     X = torch.zeros_like(B)
     run_iterations(dm, J, ilu, p, B, X, 3)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 3, ilu.color_host)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)

@@ -60,8 +60,7 @@ def test_truncated_relax_f64_matches_oracle(dims, block, N, parts):
     X = torch.from_numpy(x0.copy()).cuda()
     fnlh.fnlh_relax(dm, J, p.omega, B, X, 25, fnlh.FNLH_F64)
     ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 25, X0=x0, part=part)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_single_node_partitions_and_periodic_edges():
@@ -74,8 +73,7 @@ def test_single_node_partitions_and_periodic_edges():
     X = torch.zeros_like(B)
     fnlh.fnlh_relax(dm, J, p.omega, B, X, 3, fnlh.FNLH_F64, sigma=p.phase)
     ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 1, sigma=p.phase, part=part)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_one_partition_equals_untruncated_bitwise():
@@ -113,7 +111,7 @@ def test_partitioned_solve_reaches_full_solution(prec):
                                               flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     true_rel = oracle.rel_residuals(oracle_jac(p), p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-    assert np.all(true_rel <= 1.05e-8), true_rel
+    assert np.all(true_rel <= 1e-8), true_rel
 
 
 def test_fp64_defect_correction_matches_oracle_composition():
@@ -134,8 +132,7 @@ def test_fp64_defect_correction_matches_oracle_composition():
     for _ in range(checks - 1):
         _, r = oracle.residual(oj, p.mesh.vol, p.omega, p.b, x, want_r=True)
         x = x + oracle.jacobi(oj, p.mesh.vol, p.omega, r, inner, part=part)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), x, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), x, p.n_harm)
 
 
 def test_partitioned_batched_rows_match_per_row():
@@ -170,5 +167,4 @@ def test_full_size_truncated_relax_matches_oracle():
     x = X.cpu().numpy()
     del dm, J, B, X
     ref = oracle.jacobi(oracle_jac(p), p.mesh.vol, p.omega, p.b, 50, part=part)
-    err = _gpu.rel_err_per_system(x, ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(x, ref, p.n_harm)

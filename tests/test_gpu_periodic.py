@@ -57,8 +57,7 @@ def test_periodic_relax_f64_isolated(key):
     X = torch.from_numpy(x0.copy()).cuda()
     fnlh.fnlh_relax(dm, J, p.omega, B, X, 20, fnlh.FNLH_F64, sigma=p.phase)
     ref = oracle.jacobi(oj, p.mesh.vol, p.omega, p.b, 20, X0=x0, sigma=p.phase)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 @pytest.mark.parametrize("key", sorted(CASES))
@@ -68,8 +67,7 @@ def test_periodic_relax_f64_end_to_end(key):
     X = torch.zeros_like(B)
     fnlh.fnlh_relax(dm, J, p.omega, B, X, 40, fnlh.FNLH_F64, sigma=p.phase)
     ref = oracle.jacobi(oracle_jac(p), p.mesh.vol, p.omega, p.b, 40, sigma=p.phase)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
 
 
 def test_periodic_residual_matches_oracle():
@@ -124,7 +122,7 @@ def test_periodic_solve_reaches_1e8(prec):
                                               flags=fnlh.FNLH_SOLVE_ZERO_GUESS, sigma=p.phase)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     true_rel = oracle.rel_residuals(oracle_jac(p), p.mesh.vol, p.omega, p.b, X.cpu().numpy(), sigma=p.phase)
-    assert np.all(true_rel <= 1.05e-8), true_rel
+    assert np.all(true_rel <= 1e-8), true_rel
 
 
 def test_periodic_permuted_numbering():
@@ -135,8 +133,7 @@ def test_periodic_permuted_numbering():
     X = torch.zeros_like(B)
     fnlh.fnlh_relax(dm, J, pp.omega, B, X, 25, fnlh.FNLH_F64, sigma=pp.phase)
     ref = oracle.jacobi(oracle_jac(p), p.mesh.vol, p.omega, p.b, 25, sigma=p.phase)
-    err = _gpu.rel_err_per_system(X.cpu().numpy(), ref[perm], p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(X.cpu().numpy(), ref[perm], p.n_harm)
 
 
 @pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_F64])
@@ -160,8 +157,7 @@ def test_periodic_batched_rows_match_per_row(prec):
     for X, ref, (p, *_rest) in zip(Xs, singles, dev):
         if prec == fnlh.FNLH_F64:
             # the single-row FP64 kernel solves the mean flow with a real-only path
-            err = _gpu.rel_err_per_system(X.cpu().numpy(), ref, p.n_harm)
-            assert np.all(err <= 1e-13), err
+            _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm, tol=1e-13)
         else:
             assert np.array_equal(X.cpu().numpy(), ref)
 
@@ -203,13 +199,11 @@ def test_periodic_full_size_equals_ring():
     x = X.cpu().numpy()
     del dm, J, B, X
     ref = oracle.jacobi(oracle_jac(p), p.mesh.vol, p.omega, p.b, 50, sigma=sigma)
-    err = _gpu.rel_err_per_system(x, ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(x, ref, p.n_harm)
     ring = inputs.Problem(_ring(p, P), np.tile(p.q, (P, 1)), _phase_shift(p.b, sigma, P), p.omega, p.block, p.cfl)
     rdm, rJ, rB = _gpu.device_problem(ring, prep_flags=fnlh.FNLH_PREP_F64)
     RX = torch.zeros_like(rB)
     fnlh.fnlh_relax(rdm, rJ, ring.omega, rB, RX, 50, fnlh.FNLH_F64)
     ref = _phase_shift(x, sigma, P)
-    err = _gpu.rel_err_per_system(RX.cpu().numpy(), ref, p.n_harm)
-    assert np.all(err <= 1e-12), err
+    _gpu.assert_fp64_parity(RX.cpu().numpy(), ref, p.n_harm)
     torch.cuda.synchronize()
