@@ -1,19 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the shared-Jacobian FNLH relaxation on GB300.
 
-Workload (the FP64 GPU baseline of the measurement plan): a 128x64x48
-perturbed hex passage (393,216 nodes, 1,162,240 edges), 6x6 blocks (Euler +
-one turbulence equation), mean flow + 4 harmonics at omega_n = n, CFL 20.
-One step = assemble J and D (+ Hessenberg prep) -> 50 FP64 block-Jacobi
-sweeps over all 5 systems -> FP64 residual norms.  value = node-system
-updates per second (n K sweeps / step time), whole job.
+The metric has two halves, both on the one JSON line:
 
-Extra sections on the same line: the mixed-precision defect correction vs
-plain FP64 time to a 1e-8 relative residual (2.1M-node passage, 8
-harmonics), the batched multi-row form (three blade rows of 200k/600k/
+* value -- node-system updates per second per Jacobi sweep on the FP64 GPU
+  baseline: a 128x64x48 perturbed hex passage (393,216 nodes, 1,162,240
+  edges), 6x6 blocks (Euler + one turbulence equation), mean flow + 4
+  harmonics at omega_n = n, CFL 20.  One step = assemble J and D (+ the
+  per-node Schur prep) -> 50 FP64 block-Jacobi sweeps over all 5 systems ->
+  FP64 residual norms; value = n K sweeps / step time, whole job.  Its
+  roofline is the FP64 sweep kernel against the FP64 multiply-add peak that
+  the probe in libfnlh_probe.so measures in the same run.
+* time_to_1e8 -- mixed vs FP64 time to a 1e-8 relative FP64 residual on the
+  2.1M-node passage with 8 harmonics (FP64 Jacobi; FP64 defect correction
+  with FP32 and BF16 blocks), device-resident and end to end through the
+  public API, each solution's residual and error against the oracle's
+  solution, and the oracle's own time on the host cores.
+
+Extra sections: the batched multi-row form (three blade rows of 200k/600k/
 1.1M nodes with 2/8/4 harmonics) against per-row launches, five RK(5,3)
-stages with the paper's linear-solve rule, phase-lagged periodic edges on
-the measured passage, and an 8M-node passage with 16 harmonics.
+stages with the paper's linear-solve rule, phase-lagged periodic edges, the
+partitioned (domain-truncated) solve, ILU(0) against Jacobi, a randomly
+renumbered mesh, and an 8M-node passage with 16 harmonics.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fnlh|reference]
 """
@@ -39,12 +47,52 @@ UNIT = "updates/s"
 SWEEPS = 50
 WORKLOAD = "c2"
 
-# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM bytes (read + write) per launch of the top kernel from the last ncu
-# capture of the kernel as it stands on this workload (profiles/k_sweep_f64_c2.md);
-# to be reset to None whenever the kernel changes
-NCU_TRAFFIC = {"k_sweep_f64_c2": 1363095000 + 178223360}
+# FP64 peak from unit counts and clocks (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz): context only; the
+# roofline is taken against the FP64 peak the multiply-add probe measures on the same GPU in the same run
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
+# DRAM bytes (read + write) per launch of the top kernel from an ncu capture (profiles/k_sweep_f64_c2.md),
+# valid only while the kernel's sources hash to the value they had when it was taken
+NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363265536 + 177648896,
+                                  "sources_sha256": "e51e074e50dafa866d2415c35ecd75f1d32d3e01a082afa08c1a47f00522a363"}}
+KERNEL_SOURCES = ("paper_2404_01407_gb300/csrc/sweep.cu", "paper_2404_01407_gb300/csrc/sweep_kernel.cuh",
+                  "paper_2404_01407_gb300/csrc/common.cuh", "include/fnlh.h")
+
+
+def kernel_sources_sha256():
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(key):
+    """(bytes per launch, note): the captured DRAM bytes, or None once the sources changed."""
+    rec = NCU_TRAFFIC.get(key)
+    if not rec or rec["bytes"] is None:
+        return None, "no capture on record"
+    if rec["sources_sha256"] != kernel_sources_sha256():
+        return None, "kernel sources changed since the capture"
+    return rec["bytes"], "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/k_sweep_f64_c2.md)"
+
+
+def measure_arith_peaks(torch, dev, index):
+    """FP64 and FP32 multiply-add peaks of this GPU from the probe in libfnlh_probe.so, with the SM clock
+    sampled while it runs (outside every timed region)."""
+    from paper_2404_01407_gb300 import peaks
+
+    ck = ClockSampler(index)
+    ck.start()
+    f64, s64 = peaks.fma_tflops(torch, dev, 0)
+    f32, s32 = peaks.fma_tflops(torch, dev, 1)
+    torch.cuda.synchronize()
+    clocks = ck.stop()
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "fp64_shape": s64, "fp32_shape": s32, "clocks": clocks,
+            "source": "measured: multiply-add accumulators on every SM (libfnlh_probe.so, include/fnlh_probe.h), "
+                      "best over chain counts, operand reuse 1/2/4 (the sweeps' pattern is 2) and 256/1024-thread "
+                      "blocks, SM clock sampled meanwhile"}
 
 
 def tri_solve_flops(b: int, real: bool) -> int:
@@ -193,6 +241,53 @@ def cpu_oracle_rate(p, budget_s=15.0, max_sweeps=100):
                               "sample": f"{S1} FP64 Jacobi sweeps, {t_1:.1f} s"}}
 
 
+def cpu_oracle_large(max_sweeps=3):
+    """The oracle on the 8M-node passage (256x200x156, b = 6), a bounded sample: Jacobian build and
+    `max_sweeps` FP64 Jacobi sweeps with the mean flow and one harmonic; its cost is linear in the number
+    of systems, so the per-sweep time of the 17-system case is extrapolated from the update rate."""
+    import oracle
+    from paper_2404_01407_gb300 import inputs
+
+    c = inputs.CONFIGS["c5"]
+    p = inputs.config_problem("c5", n_harm=1)
+    m = p.mesh
+    t0 = time.perf_counter()
+    oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.jacobi(oj, m.vol, p.omega, p.b, max_sweeps)
+    t = time.perf_counter() - t0
+    rate = m.n_nodes * 2 * max_sweeps / t
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"c5 full mesh ({m.n_nodes} nodes), mean + 1 harmonic, {max_sweeps} FP64 Jacobi sweeps, "
+                      f"{t:.1f} s (build {t_build:.1f} s excluded)",
+            "build_seconds": t_build,
+            "extrapolated_seconds_per_sweep_N16": m.n_nodes * (1 + c["n_harm"]) / rate,
+            "note": "per-sweep time at 16 harmonics extrapolated from the update rate at 1 (linear in systems)"}
+
+
+def stress_permuted_section(torch, fnlh, inputs, dev):
+    """Locality stress: the measured passage with its nodes randomly renumbered (seed 4) against the
+    lexicographic numbering -- sweep times per precision."""
+    p = inputs.config_problem(WORKLOAD)
+    mesh, perm = inputs.permute_mesh(p.mesh, seed=4)
+    out = {"workload": f"{WORKLOAD}: lexicographic vs randomly renumbered (seed 4) nodes, sweep time"}
+    for tag, m, q, b in (("lexicographic", p.mesh, p.q, p.b), ("permuted", mesh, p.q[perm], p.b[perm])):
+        dm = fnlh.DeviceMesh.from_mesh(m, dev)
+        J = fnlh.DeviceJacobian(dm, p.block, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16, dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(q).to(dev), fnlh.make_params(p.cfl), J)
+        B = torch.from_numpy(b).to(dev)
+        X = torch.zeros_like(B)
+        ws = fnlh.workspace(m.n_nodes, p.block, p.n_harm, dev)
+        out[tag] = {name + "_sweep_ms": sweep_time_ms(torch, fnlh, dm, J, p, B, X, ws, prec)
+                    for name, prec in (("f64", fnlh.FNLH_F64), ("f32", fnlh.FNLH_F32), ("bf16", fnlh.FNLH_BF16))}
+        del dm, J, B, X, ws
+        torch.cuda.empty_cache()
+    for name in ("f64", "f32", "bf16"):
+        out[f"{name}_slowdown"] = out["permuted"][f"{name}_sweep_ms"] / out["lexicographic"][f"{name}_sweep_ms"]
+    return out
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if world > 1:
@@ -207,23 +302,25 @@ def run_reference(args):
     p = inputs.config_problem(args.workload)
     m = p.mesh
     K = 1 + p.n_harm
-    oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
-    sweeps_per_step = 2
-    X = np.zeros_like(p.b)
+
+    def step():  # the GPU arm's step: assemble J and D, SWEEPS FP64 block-Jacobi sweeps, residual
+        oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+        X = oracle.jacobi(oj, m.vol, p.omega, p.b, SWEEPS)
+        oracle.residual(oj, m.vol, p.omega, p.b, X)
+
     for _ in range(args.warmup):
-        X = oracle.jacobi(oj, m.vol, p.omega, p.b, sweeps_per_step, X0=X)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        X = oracle.jacobi(oj, m.vol, p.omega, p.b, sweeps_per_step, X0=X)
-        oracle.residual(oj, m.vol, p.omega, p.b, X)
+        step()
     t = time.perf_counter() - t0
-    value = m.n_nodes * K * sweeps_per_step * args.steps / t
-    sample = (f"{args.workload} full mesh; each step {sweeps_per_step} FP64 Jacobi sweeps + 1 residual "
-              f"(Jacobian built once, untimed)")
+    value = m.n_nodes * K * SWEEPS * args.steps / t
+    sample = (f"{args.workload} full mesh; each step the GPU arm's step: Jacobian build + {SWEEPS} FP64 "
+              f"Jacobi sweeps + 1 residual")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p, sweeps_per_step),
+            "data": "synthetic", "config": workload_config(p),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -311,15 +408,7 @@ def run_fnlh(args):
     flops = sweep_flops(n, nnz, b, N, block_entries=(b * b - (b - 1)) if structured else None)
     achieved = flops / (sweep_ms * 1e-3)
     bytes_alg = sweep_bytes(n, nnz, b, N, 8, 8, 8, 8)
-    roofline = {"bound": "alu", "kernel": "k_sweep_f64<6> (FP64 fused sweep)",
-                "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_FLOPS,
-                "traffic": NCU_TRAFFIC.get(f"k_sweep_f64_{args.workload}"),
-                "peak_note": "FP64 peak from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
-                             "not in MEASURED_PEAKS.json",
-                "sweep_ms": sweep_ms, "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
-                "hbm_gbs_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9,
-                "hbm_frac_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    traffic, traffic_note = ncu_traffic(f"k_sweep_f64_{args.workload}")
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region.  The
     # copies run on a second stream, double-buffered: step s+1's inputs go up while step s computes, and
@@ -384,6 +473,20 @@ def run_fnlh(args):
            "h2d_bytes_per_step": Qh.numel() * 8 + Bh.numel() * 8,
            "d2h_bytes_per_step": Xh.numel() * 8 + nh.numel() * 8, "ms_per_step": e2e_ms}
 
+    # the FP64 peak the sweep is bound by, measured now (after the timed regions)
+    arith = measure_arith_peaks(torch, dev, local)
+    peak = arith["fp64_tflops"] * 1e12
+    roofline = {"bound": "alu", "kernel": "k_sweep_f64<6> (FP64 fused sweep)",
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "traffic_note": traffic_note,
+                "peak_source": arith["source"], "peak_probe": {k: arith[k] for k in ("fp64_shape", "clocks")},
+                "peak_note": f"derived from unit counts and clocks: {FP64_PEAK_DERIVED / 1e12:.3f} TFLOP/s "
+                             "(152 SMs x 2 FP64 FMA/clk x 2.07 GHz); MEASURED_PEAKS.json has no FP64 figure",
+                "frac_of_derived": achieved / FP64_PEAK_DERIVED,
+                "sweep_ms": sweep_ms, "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+                "hbm_gbs_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9,
+                "hbm_frac_alg": bytes_alg / (sweep_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded perturbed hex passage, flow state and right-hand sides)",
@@ -392,11 +495,12 @@ def run_fnlh(args):
             "final_rel_residual": [float(x) for x in rel],
             "final_rel_residual_Rz": float(np.sqrt(np.mean(np.square(rel)))), "peaks_source": peaks_kind}
 
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1:
         del J, ws
         torch.cuda.empty_cache()
-        line["mixed_vs_fp64"] = mixed_section(torch, fnlh, inputs, dev)
+        line["time_to_1e8"] = time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=not args.no_cpu)
         torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_extras:
         line["batched"] = batched_section(torch, fnlh, inputs, dev, args)
         torch.cuda.empty_cache()
         line["batched_small_rows"] = batched_small_section(torch, fnlh, inputs, dev)
@@ -407,12 +511,16 @@ def run_fnlh(args):
         torch.cuda.empty_cache()
         line["partitions"] = partition_section(torch, fnlh, inputs, dev)
         torch.cuda.empty_cache()
-        line["ilu_vs_jacobi"] = ilu_section(torch, fnlh, inputs, dev)
+        line["ilu_vs_jacobi"] = ilu_section(torch, fnlh, inputs, dev, arith)
+        torch.cuda.empty_cache()
+        line["stress_permuted"] = stress_permuted_section(torch, fnlh, inputs, dev)
         if not args.no_large:
             torch.cuda.empty_cache()
             line["large"] = large_section(torch, fnlh, inputs, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(p)
+        if not args.no_large:
+            line["cpu_baseline"]["large"] = cpu_oracle_large()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -420,23 +528,33 @@ def run_fnlh(args):
         dist.destroy_process_group()
 
 
-def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
-    """Plain FP64 Jacobi vs defect correction (FP32 / BF16 blocks) to a 1e-8 FP64 residual."""
+def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
+    """The metric's second half on the mixed-precision workload (160x128x102, 2.1M nodes, mean + 8
+    harmonics): time to a 1e-8 relative FP64 residual for plain FP64 Jacobi (residual every 10 sweeps)
+    and FP64 defect correction with FP32 and BF16 blocks.  Per precision: device-resident time, the
+    same through the public API with B copied in from pinned host memory and x copied out, the residual
+    the library reports per system, the oracle's FP64 residual of the returned x per system, and each
+    system's error against the oracle's own solution (plain FP64 Jacobi to the same tolerance and check
+    cadence on the host cores, whose time is reported too)."""
     p = inputs.config_problem("c3")
     n, b, N = p.mesh.n_nodes, p.block, p.n_harm
     dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
     flags = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
     J = fnlh.DeviceJacobian(dm, b, flags, dev)
     fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
-    B = torch.from_numpy(p.b).to(dev)
+    Bh = torch.from_numpy(p.b).pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
+    B = Bh.to(dev)
     X = torch.zeros_like(B)
     ws = fnlh.workspace(n, b, N, dev)
-    out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, b=6, mean + {N} harmonics, CFL 20, tol {tol:g}"}
+    out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, {p.mesh.n_edges} edges, b=6, mean + {N} "
+                       f"harmonics, CFL 20, to a {tol:g} relative FP64 residual per system, from zero",
+           "unit": "s", "higher_is_better": False}
     # inner sweeps per FP64 residual: the best of a scan of 10..40 on this workload (every run needs
     # ~60 sweeps; each extra check costs one FP64 residual)
     cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)]
     zg = fnlh.FNLH_SOLVE_ZERO_GUESS
-    x64 = None
+    sols = {}
     for name, prec, inner in cases:
         fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)  # warm
         torch.cuda.synchronize()
@@ -445,20 +563,25 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
                                                   raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
+        # end to end through the public API: B up from pinned host memory, the solve, x down
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.copy_(Bh, non_blocking=True)
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=ws, raise_on_error=False, flags=zg)
+        Xh.copy_(X, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        sols[name] = Xh.numpy().copy()
         out[name] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
                      "inner_sweeps": inner, "max_rel_residual": float(np.max(rel)),
-                     "rel_residual_per_system": [float(v) for v in rel]}
-        # per-system error against the FP64 solution (itself at 1e-12 of the oracle), both at 1e-8 residual
-        if x64 is None:
-            x64 = X.clone()
-        else:
-            cols = [[0]] + [[2 * k - 1, 2 * k] for k in range(1, N + 1)]
-            out[name]["rel_error_vs_fp64_per_system"] = [
-                float(torch.linalg.vector_norm(X[:, c] - x64[:, c]) / torch.linalg.vector_norm(x64[:, c]))
-                for c in cols]
+                     "rel_residual_per_system": [float(v) for v in rel],
+                     "e2e": {"seconds": e0.elapsed_time(e1) * 1e-3, "h2d_bytes": Bh.numel() * 8,
+                             "d2h_bytes": Xh.numel() * 8}}
     if out["f64"]["status"] == "success":
         for name in ("f32", "bf16"):
             out[name]["speedup_vs_f64"] = out["f64"]["seconds"] / out[name]["seconds"]
+            out[name]["e2e_speedup_vs_f64"] = out["f64"]["e2e"]["seconds"] / out[name]["e2e"]["seconds"]
     # the inner sweep alone: HBM roofline (algorithmic bytes, FP32 iterate)
     peaks, _ = load_peaks()
     nnz = 2 * p.mesh.n_edges
@@ -468,7 +591,31 @@ def mixed_section(torch, fnlh, inputs, dev, tol=1e-8):
         out[name]["inner_sweep"] = {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
                                     "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                     "frac_hbm_nominal_7900": alg / (ms * 1e-3) / 1e9 / 7900.0}
-    del x64
+    del dm, J, B, X, ws
+    torch.cuda.empty_cache()
+    if with_oracle:
+        import oracle
+
+        m = p.mesh
+        t0 = time.perf_counter()
+        oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+        t_build = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        xo, osw = oracle.solve_to_tol(oj, m.vol, p.omega, p.b, tol=tol, chunk=10)
+        t_solve = time.perf_counter() - t0
+        orel = oracle.rel_residuals(oj, m.vol, p.omega, p.b, xo)
+        out["oracle"] = {"seconds": t_solve, "build_seconds": t_build, "sweeps": osw, "checks_every": 10,
+                         "cores": oracle.num_threads(), "kind": "oracle (plain FP64 block Jacobi, C, OpenMP)",
+                         "rel_residual_per_system": [float(v) for v in orel]}
+        cols = [[0]] + [[2 * k - 1, 2 * k] for k in range(1, N + 1)]
+        for name in ("f64", "f32", "bf16"):
+            x = sols[name]
+            out[name]["oracle_rel_residual_per_system"] = [
+                float(v) for v in oracle.rel_residuals(oj, m.vol, p.omega, p.b, x)]
+            out[name]["rel_error_vs_oracle_per_system"] = [
+                float(np.linalg.norm(x[:, c] - xo[:, c]) / np.linalg.norm(xo[:, c])) for c in cols]
+            out[name]["speedup_vs_oracle"] = t_solve / out[name]["seconds"]
+        del oj, xo
     return out
 
 
@@ -552,11 +699,13 @@ def periodic_section(torch, fnlh, inputs, dev):
     return out
 
 
-def ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, reps=3):
+def ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, arith, reps=3):
     """Colour passes of one ILU(0) iteration (forward + backward, all colours):
     CUDA-event time on the launching stream (the library's timing hook brackets
     the passes of the last iteration), algorithmic flops and bytes per
-    iteration, and their fractions of the FP64 peak and the measured HBM peak."""
+    iteration, and their fractions of the measured arithmetic peak of the
+    passes' own precision (FP64 or FP32, from the multiply-add probe) and of
+    the measured HBM peak."""
     n, b, N = p.mesh.n_nodes, p.block, p.n_harm
     K, C = 1 + N, 1 + 2 * N
     nnz = 2 * p.mesh.n_edges
@@ -585,12 +734,17 @@ def ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, reps=3):
     fnlh.fnlh_set_sweep_events(None, None)
     ms = sum(a.elapsed_time(z) for a, z in ev) / reps
     peaks, _ = load_peaks()
-    return {"ms": ms, "flops": flops, "alg_bytes": bytes_, "tflops": flops / (ms * 1e-3) / 1e12,
-            "frac_fp64_peak": flops / (ms * 1e-3) / FP64_PEAK_FLOPS, "gbs": bytes_ / (ms * 1e-3) / 1e9,
-            "frac_hbm": bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    tflops = flops / (ms * 1e-3) / 1e12
+    out = {"ms": ms, "flops": flops, "alg_bytes": bytes_, "tflops": tflops, "gbs": bytes_ / (ms * 1e-3) / 1e9,
+           "frac_hbm": bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    if prec == fnlh.FNLH_F64:
+        out["frac_fp64_peak"] = tflops / arith["fp64_tflops"]
+    else:
+        out["frac_fp32_peak"] = tflops / arith["fp32_tflops"]
+    return out
 
 
-def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
+def ilu_section(torch, fnlh, inputs, dev, arith, tol=1e-8):
     """The paper's smoother, block ILU(0) in red-black order, against block
     Jacobi on the measured passage: iterations and time to a 1e-8 FP64
     residual, and the paper's stage rule (1e-2 drop from zero, at most 10)."""
@@ -623,7 +777,7 @@ def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
         out[name] = {"colors": ilu.n_colors, "factor_seconds": tf, "status": fnlh.fnlh_strerror(st),
                      "iterations": its, "seconds": t, "max_rel_residual": float(np.max(rel)),
                      "stage_rule_iterations": its2, "factor_bytes": int(ilu.factor.numel()),
-                     "passes": ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec)}
+                     "passes": ilu_pass_roofline(torch, fnlh, dm, J, ilu, p, B, X, ws, prec, arith)}
         del ilu
         torch.cuda.empty_cache()
     # the colour passes read every array in colour order: with the nodes
@@ -641,7 +795,7 @@ def ilu_section(torch, fnlh, inputs, dev, tol=1e-8):
                                                               flags=zg, raise_on_error=False))
         out[name] = {"status": fnlh.fnlh_strerror(st), "iterations": its, "seconds": t,
                      "max_rel_residual": float(np.max(rel)),
-                     "passes": ilu_pass_roofline(torch, fnlh, dmc, Jc, ilu, p, Bc, X, ws, prec)}
+                     "passes": ilu_pass_roofline(torch, fnlh, dmc, Jc, ilu, p, Bc, X, ws, prec, arith)}
         del ilu
     del dmc, Jc, Bc
     torch.cuda.empty_cache()

@@ -1,4 +1,6 @@
-"""Build libfnlh.so (the CUDA library) in-tree with nvcc for sm_103a.
+"""Build libfnlh.so (the CUDA library) in-tree with nvcc for sm_103a, and
+beside it libfnlh_probe.so (the arithmetic peak probe the benchmark reports
+its FP64 roofline against).
 
 Each translation unit is compiled in parallel, then linked against the shared
 CUDA runtime (the same libcudart the host process already uses).
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfnlh.so")
+PROBE_DIR = os.path.join(PKG, "probe")
+PROBE_LIB = os.path.join(PKG, "libfnlh_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -56,22 +60,34 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libfnlh.so if any source or header is newer."""
-    srcs = sources()
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= _newest(srcs + headers() + [__file__])):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+def _link(objs, out):
+    tmp = out + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile and link libfnlh.so and libfnlh_probe.so if any source or header is newer."""
+    srcs = sources()
+    probe_srcs = sorted(os.path.join(PROBE_DIR, f) for f in os.listdir(PROBE_DIR) if f.endswith(".cu"))
+    deps = headers() + [__file__]
+    need_lib = force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(srcs + deps)
+    need_probe = (force or not os.path.exists(PROBE_LIB)
+                  or os.path.getmtime(PROBE_LIB) < _newest(probe_srcs + deps))
+    if not (need_lib or need_probe):
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
+    todo = (srcs if need_lib else []) + (probe_srcs if need_probe else [])
+    with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
+        objs = dict(zip(todo, ex.map(lambda s_: _compile(s_, extra), todo)))
+    if need_lib:
+        _link([objs[s_] for s_ in srcs], LIB)
+    if need_probe:
+        _link([objs[s_] for s_ in probe_srcs], PROBE_LIB)
     return LIB
 
 

@@ -1,7 +1,7 @@
 // Fused block-Jacobi sweep over the mean flow and every harmonic.
 //
-// Paper: arXiv 2404.01407, "Solution Update" -- the block-diagonal inversion
-// "performed point by point" (block Jacobi) of Eq. lhs_mean / Eq. lhs_lin with
+// Paper: arXiv 2404.01407, "Solution Update" -- the block-diagonal inversion,
+// node by node (block Jacobi), of Eq. lhs_mean / Eq. lhs_lin with
 // the harmonic LHS of Eq. precon_linear, K_l = K + i omega_l V I, sharing one
 // J across all systems:
 //   x_i <- (J_ii + (D_i + i omega_k V_i) I)^-1 (B_i - sum_j J_ij x_j).

@@ -221,17 +221,21 @@ def test_ilu_sizes_and_validation():
 
 def test_probe_library_exports_every_declared_symbol():
     """The peak probe beside the library (include/fnlh_probe.h) builds and
-    exports its declared symbols; argument checks need no GPU."""
+    exports its declared symbols; bad arguments are rejected on the host,
+    before any launch (no GPU needed)."""
     from paper_2404_01407_gb300 import peaks
 
     text = open(os.path.join(ROOT, "include", "fnlh_probe.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     declared = sorted(set(re.findall(r"\b(fnlh_\w+)\s*\(", text)))
-    assert declared == ["fnlh_probe_chains", "fnlh_probe_fma", "fnlh_probe_threads_per_block"]
+    assert declared == ["fnlh_probe_fma"]
     lib = peaks.probe_lib()
-    for name in declared:
-        assert hasattr(lib, name), name
-    assert lib.fnlh_probe_threads_per_block() == 256 and lib.fnlh_probe_chains() == 8
+    assert hasattr(lib, "fnlh_probe_fma")
     ms = ctypes.c_float(0.0)
-    assert lib.fnlh_probe_fma(2, 1, 1, None, ctypes.byref(ms), None) == -1  # bad precision: rejected on the host
-    assert lib.fnlh_probe_fma(0, 0, 1, None, ctypes.byref(ms), None) == -1
+    sink = ctypes.c_void_p(16)  # never dereferenced: every call below fails its argument check
+    assert lib.fnlh_probe_fma(2, 8, 1, 1, 256, 1, sink, ctypes.byref(ms), None) == -1  # precision
+    assert lib.fnlh_probe_fma(0, 5, 1, 1, 256, 1, sink, ctypes.byref(ms), None) == -1  # chains
+    assert lib.fnlh_probe_fma(0, 8, 3, 1, 256, 1, sink, ctypes.byref(ms), None) == -1  # reuse
+    assert lib.fnlh_probe_fma(0, 8, 1, 1, 100, 1, sink, ctypes.byref(ms), None) == -1  # threads
+    assert lib.fnlh_probe_fma(0, 8, 1, 0, 256, 1, sink, ctypes.byref(ms), None) == -1  # blocks
+    assert lib.fnlh_probe_fma(0, 8, 1, 1, 256, 1, None, ctypes.byref(ms), None) == -1  # sink
