@@ -158,9 +158,16 @@ typedef struct fnlh_row {
 /* Launch shape of the batched sweep kernel (0 = library default). */
 typedef struct fnlh_tuning {
     int32_t threads;      /* threads per CTA = (node, system) pairs per tile; 32..256, multiple of 32 */
-    int32_t ctas_per_sm;  /* 0: one CTA per tile; > 0: persistent grid of SMs x this CTAs */
+    int32_t ctas_per_sm;  /* 0: one CTA per tile; > 0: persistent grid of SMs x this CTAs;
+                             FNLH_TUNING_PER_ROW: every row its own single-row launches (threads unused) */
     int32_t reserved[2];
 } fnlh_tuning;
+
+/* fnlh_tuning.ctas_per_sm: rows large enough to fill the GPU on their own
+ * gain nothing from sharing a launch, and the single-row kernels are the
+ * faster ones for them (the FP64 one solves the mean flow on a real-only
+ * path); the autotuner weighs this mode against the shared launches. */
+#define FNLH_TUNING_PER_ROW (-1)
 
 /* Human-readable text of a status code (static storage). */
 const char *fnlh_strerror(int status);

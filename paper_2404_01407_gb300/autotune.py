@@ -1,10 +1,12 @@
 """Autotuner for the launch shape of the batched persistent sweep.
 
 Searches threads per CTA (= (node, system) pairs per tile) and the grid shape
-(one CTA per tile, or a persistent grid of SMs x ctas_per_sm CTAs) by timing
-the real kernel with CUDA events, and caches the winner per problem signature
-(block size, per-row systems, node-count bucket, precision, SM count) in a
-JSON file next to the library (git-ignored).
+(one CTA per tile, or a persistent grid of SMs x ctas_per_sm CTAs), and the
+per-row mode (every row its own single-row launches: rows that fill the GPU
+on their own gain nothing from sharing one), by timing the real calls with
+CUDA events, and caches the winner per problem signature (block size,
+per-row systems, node-count bucket, precision, SM count) in a JSON file next
+to the library (git-ignored).
 """
 
 from __future__ import annotations
@@ -46,6 +48,7 @@ def candidates():
     for th in SEARCH_THREADS:
         for c in SEARCH_CTAS_PER_SM:
             yield fnlh.fnlh_tuning(th, c)
+    yield fnlh.fnlh_tuning(0, fnlh.FNLH_TUNING_PER_ROW)
 
 
 def tune_batched(time_ms, key=None, use_cache=True):

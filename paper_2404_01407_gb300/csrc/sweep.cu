@@ -753,6 +753,60 @@ int batch_launch(BatchArgs& a, const BatchPlan& P, int sweeps, int x_zero, cudaS
 
 static thread_local BatchArgs g_batch;  // large: kept off the stack (each launch copies it)
 
+static bool per_row_mode(const fnlh_tuning* tn) { return tn && tn->ctas_per_sm == FNLH_TUNING_PER_ROW; }
+
+// Per-row mode: the single-row sweep of every row in turn (each row's rows
+// of the workspace as batch_setup lays them out), `sweeps` from its x.
+template <int BS, typename TJ, typename T>
+int batched_per_row(const fnlh_row* rows, int n_rows, int sweeps, const BatchArgs& a, const BatchPlan& P,
+                    cudaStream_t s) {
+  int rc = mark(g_ev_begin, s);
+  if (rc) return rc;
+  for (int r = 0; r < n_rows; ++r) {
+    const BatchRow& D = a.row[r];
+    double* pivinv = nullptr;
+    if constexpr (sizeof(T) == 8) {
+      pivinv = at<double>(P.base[r], ws_layout(D.row.n, BS, D.row.K - 1, FNLH_F64).pivinv);
+      if ((rc = pivot_inverses<BS>(rows[r].mesh, (const double*)P.ops[r].hess, P.sys[r], pivinv, s))) return rc;
+    }
+    T* res = nullptr;
+    // the timing hook brackets the whole batch, not each row's sweeps
+    cudaEvent_t b = g_ev_begin, e = g_ev_end;
+    g_ev_begin = g_ev_end = nullptr;
+    rc = run_sweeps<BS, TJ, T>(rows[r].mesh, P.ops[r], P.sys[r], (const T*)D.row.Bt, (T*)D.x[0], (T*)D.x[1], sweeps,
+                               0, s, &res, D.masked ? D.active : nullptr, pivinv);
+    g_ev_begin = b;
+    g_ev_end = e;
+    if (rc) return rc;
+    if ((rc = rotate_out<BS, T>(D.row.n, D.row.K, P.ops[r].rot, res, rows[r].X, 0, s))) return rc;
+  }
+  return mark(g_ev_end, s);
+}
+
+// Per-row mode of the batched solve: `sweeps` single-row sweeps of every row
+// between its ping-pong buffers, from a.parity (from zero when x_zero); the
+// result is in D.x[a.parity] on return, as after batch_launch.
+template <int BS, typename TJ, typename T>
+int sweep_rows_per_row(const fnlh_row* rows, int n_rows, int sweeps, int x_zero, BatchArgs& a, const BatchPlan& P,
+                       double* const* pivinv, cudaStream_t s) {
+  int rc = mark(g_ev_begin, s);
+  if (rc) return rc;
+  cudaEvent_t b = g_ev_begin, e = g_ev_end;
+  g_ev_begin = g_ev_end = nullptr;
+  for (int r = 0; r < n_rows && !rc; ++r) {
+    const BatchRow& D = a.row[r];
+    T* res = nullptr;
+    rc = run_sweeps<BS, TJ, T>(rows[r].mesh, P.ops[r], P.sys[r], (const T*)D.row.Bt, (T*)D.x[a.parity],
+                               (T*)D.x[a.parity ^ 1], sweeps, x_zero, s, &res, D.masked ? D.active : nullptr,
+                               pivinv[r]);
+  }
+  g_ev_begin = b;
+  g_ev_end = e;
+  if (rc) return rc;
+  a.parity ^= (sweeps & 1);
+  return mark(g_ev_end, s);
+}
+
 template <int BS, typename TJ, typename T>
 int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, const fnlh_tuning* tn, void* ws,
                   cudaStream_t s) {
@@ -760,6 +814,14 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
   BatchPlan P;
   int rc = batch_setup<BS, TJ, T>(rows, n_rows, precision, tn, ws, a, P);
   if (rc) return rc;
+  if (per_row_mode(tn)) {
+    for (int r = 0; r < n_rows; ++r) {
+      const BatchRow& D = a.row[r];
+      if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].B, (T*)D.row.Bt, s))) return rc;
+      if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].X, (T*)D.x[0], s))) return rc;
+    }
+    return batched_per_row<BS, TJ, T>(rows, n_rows, sweeps, a, P, s);
+  }
   for (int r = 0; r < n_rows; ++r) {
     const BatchRow& D = a.row[r];
     if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].B, (T*)D.row.Bt, s))) return rc;
@@ -789,6 +851,16 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
   const bool mixed = sizeof(T) == 4;
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
+  const bool per_row = per_row_mode(tn);
+  double* pivinv[kMaxBatchRows] = {};
+  if constexpr (sizeof(T) == 8) {
+    if (per_row)  // the single-row FP64 sweep reads its pivot table (fnlh_workspace_bytes at FNLH_F64 holds it)
+      for (int r = 0; r < n_rows; ++r) {
+        const BatchRow& D = a.row[r];
+        pivinv[r] = at<double>(P.base[r], ws_layout(D.row.n, BS, D.row.K - 1, FNLH_F64).pivinv);
+        if ((rc = pivot_inverses<BS>(rows[r].mesh, (const double*)P.ops[r].hess, P.sys[r], pivinv[r], s))) return rc;
+      }
+  }
   for (int r = 0; r < n_rows; ++r) {
     const BatchRow& D = a.row[r];
     if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(rows[r].X, 0, sizeof(double) * (size_t)D.row.n * P.sys[r].C * BS, s));
@@ -847,14 +919,18 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
       }
     if (mixed) {
       a.parity = 0;
-      if ((rc = batch_launch<BS, TJ, T>(a, P, inner, 1, s))) return rc;
+      if (per_row) rc = sweep_rows_per_row<BS, TJ, T>(rows, n_rows, inner, 1, a, P, pivinv, s);
+      else rc = batch_launch<BS, TJ, T>(a, P, inner, 1, s);
+      if (rc) return rc;
       for (int r = 0; r < n_rows; ++r) {
         const BatchRow& D = a.row[r];
         if ((rc = update_f32(D.row.n, D.row.K, BS, P.ops[r].rotf, (const float*)D.x[a.parity], rows[r].X, s)))
           return rc;
       }
     } else {
-      if ((rc = batch_launch<BS, TJ, T>(a, P, inner, 0, s))) return rc;
+      if (per_row) rc = sweep_rows_per_row<BS, TJ, T>(rows, n_rows, inner, 0, a, P, pivinv, s);
+      else rc = batch_launch<BS, TJ, T>(a, P, inner, 0, s);
+      if (rc) return rc;
       for (int r = 0; r < n_rows; ++r) {
         const BatchRow& D = a.row[r];
         if ((rc = rotate_out<BS, T>(D.row.n, D.row.K, P.ops[r].rot, (const T*)D.x[a.parity], rows[r].X, 0, s)))

@@ -74,6 +74,9 @@ class fnlh_tuning(ctypes.Structure):
     _fields_ = [("threads", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32 * 2)]
 
 
+FNLH_TUNING_PER_ROW = -1  # fnlh_tuning.ctas_per_sm: every row its own single-row launches
+
+
 class FnlhError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status

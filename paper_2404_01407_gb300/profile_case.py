@@ -5,6 +5,7 @@ calls, then `--reps` calls of the chosen operation, and prints their mean
 time from CUDA events.
 
   python -m paper_2404_01407_gb300.profile_case --op relax --prec bf16 --dims 96 96 64 --harm 8
+  python -m paper_2404_01407_gb300.profile_case --op batched --prec bf16 --rows 60,40,40,2 75,56,60,8 94,82,60,4
 """
 
 from __future__ import annotations
@@ -20,7 +21,7 @@ from . import fnlh, inputs
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["relax", "residual", "build", "solve", "ilu"], default="relax")
+    ap.add_argument("--op", choices=["relax", "residual", "build", "solve", "ilu", "batched"], default="relax")
     ap.add_argument("--prec", choices=list(fnlh.PRECISIONS), default="f64")
     ap.add_argument("--dims", type=int, nargs=3, default=[128, 64, 48])
     ap.add_argument("--block", type=int, default=6)
@@ -29,7 +30,13 @@ def main():
     ap.add_argument("--sweeps", type=int, default=1)
     ap.add_argument("--warm", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rows", nargs="+", default=["60,40,40,2", "75,56,60,8", "94,82,60,4"],
+                    help="--op batched: blade rows as nx,ny,nz,harmonics (row r: omega base 1 + 0.65 r)")
+    ap.add_argument("--threads", type=int, default=0, help="--op batched: fnlh_tuning.threads (0: default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="--op batched: fnlh_tuning.ctas_per_sm")
     a = ap.parse_args()
+    if a.op == "batched":
+        return batched(a)
     prec = fnlh.PRECISIONS[a.prec]
     p = inputs.problem(tuple(a.dims), a.block, a.harm, a.cfl, name="profile")
     dev = torch.device("cuda")
@@ -82,6 +89,39 @@ def main():
     if a.op == "ilu" and a.reps > 0 and a.sweeps > 0:  # the hook brackets the last iteration's passes
         out["ms_passes_per_iteration"] = sum(b.elapsed_time(e) for b, e in sw) / a.reps
     print(json.dumps(out))
+
+
+def batched(a):
+    """Blade rows through fnlh_relax_batched: `--warm` untimed calls, then
+    `--reps` timed calls of `--sweeps` sweeps each."""
+    prec = fnlh.PRECISIONS[a.prec]
+    dev = torch.device("cuda")
+    rows, keep = [], []
+    for r, spec in enumerate(a.rows):
+        nx, ny, nz, N = (int(v) for v in spec.split(","))
+        p = inputs.problem((nx, ny, nz), a.block, N, a.cfl, 1.0 + 0.65 * r, seeds=(1 + 3 * r, 2 + 3 * r, 3 + 3 * r))
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
+        J = fnlh.DeviceJacobian(dm, a.block, fnlh.PREP_FOR.get(prec, fnlh.FNLH_PREP_F64), dev)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
+        B = torch.from_numpy(p.b).to(dev)
+        X = torch.zeros_like(B)
+        rows.append((dm, J, p.omega, B, X))
+        keep.append(p.mesh.n_nodes)
+    batch = fnlh.BatchedRows(rows)
+    ws = torch.empty(batch.workspace_bytes(a.block, prec), dtype=torch.uint8, device=dev)
+    tn = fnlh.fnlh_tuning(a.threads, a.ctas_per_sm)
+    for _ in range(a.warm):
+        fnlh.fnlh_relax_batched(batch, a.sweeps, prec, tuning=tn, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        fnlh.fnlh_relax_batched(batch, a.sweeps, prec, tuning=tn, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": "batched", "prec": a.prec, "rows": a.rows, "nodes": keep,
+                      "ms_per_call": e0.elapsed_time(e1) / max(a.reps, 1),
+                      "finite": all(bool(torch.isfinite(r[4]).all()) for r in rows)}))
 
 
 if __name__ == "__main__":

@@ -154,3 +154,48 @@ def test_batched_relax_graph_replay_matches_oracle(tuning):
                 err = _gpu.rel_err_per_system(X1.cpu().numpy(), ref, p.n_harm)
                 assert np.all(err <= 5e-2), err
         del g, ws
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16, fnlh.FNLH_F64])
+def test_per_row_mode_equals_single_row_calls(prec):
+    """fnlh_tuning.ctas_per_sm = FNLH_TUNING_PER_ROW runs every row's own
+    single-row sweeps: the batched relax and the batched solve then equal the
+    per-row calls bit for bit in every precision (the FP64 one included,
+    whose shared-launch tile takes the complex path for the mean flow), also
+    when the batched relax is replayed from a CUDA graph."""
+    tn = fnlh.fnlh_tuning(0, fnlh.FNLH_TUNING_PER_ROW)
+    dev = device_rows(rows_problem())
+    sweeps = 7
+    singles = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        fnlh.fnlh_relax(dm, J, p.omega, B, X, sweeps, prec)
+        singles.append(X.clone())
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+    fnlh.fnlh_relax_batched(batch, sweeps, prec, tuning=tn, ws=ws)
+    for X, ref in zip(Xs, singles):
+        assert torch.equal(X, ref)
+    g = _capture(lambda s: fnlh.fnlh_relax_batched(batch, sweeps, prec, tuning=tn, ws=ws, stream=s))
+    for X in Xs:
+        X.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for X, ref in zip(Xs, singles):
+        assert torch.equal(X, ref)
+    del g
+    # the solve: same checks, sweeps and bits as the per-row solves
+    inner, checks = 6, 4
+    solos = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 0.0, inner, checks, raise_on_error=False)
+        solos.append(X.clone())
+    for X in Xs:
+        X.zero_()
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 0.0, inner, checks, tuning=tn, ws=ws,
+                                             raise_on_error=False)
+    assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks and sw == inner * (checks - 1)
+    for X, ref in zip(Xs, solos):
+        assert torch.equal(X, ref)

@@ -172,7 +172,8 @@ def test_batched_rows_match_per_row():
     Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
     batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
     ws = torch.empty(batch.workspace_bytes(6), dtype=torch.uint8, device="cuda")
-    for tn in (None, fnlh.fnlh_tuning(128, 2), fnlh.fnlh_tuning(256, 0)):
+    for tn in (None, fnlh.fnlh_tuning(128, 2), fnlh.fnlh_tuning(256, 0),
+               fnlh.fnlh_tuning(0, fnlh.FNLH_TUNING_PER_ROW)):
         for X in Xs:
             X.zero_()
         fnlh.fnlh_relax_batched(batch, 13, fnlh.FNLH_F32, tuning=tn, ws=ws)
