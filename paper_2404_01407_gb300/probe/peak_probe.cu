@@ -6,12 +6,14 @@
 // `iters` steps, updates acc[k][r] <- j[k] * x[r] + acc[k][r]: every j[k]
 // feeds `reuse` consecutive multiply-adds, the operand pattern of the
 // block-times-slice products of the sweeps (one block entry times the real
-// and the imaginary part of a slice).  On GB300 the FP64 rate depends on it
-// (register-file operand reads): 1.06 TFLOP/s with no reuse, 1.16 with a
-// pair.  Counted work: 2 flops x chains x reuse x iters per thread; the
-// grid is `blocks` x `threads`.  The accumulators' sum goes to `sink`
-// (caller-owned device memory, one double per thread), so nothing is removed
-// by the compiler.
+// and the imaginary part of a slice).  On GB300 the FP64 rate depends on the
+// operand pattern: about 1.06 TFLOP/s for a bare dependent chain
+// x <- x m + c, 1.16 for pairs sharing an operand, 1.23 for 8 chains x 2
+// with every operand in a register (97% of 152 SMs x 2 FMA/clk x 2.07 GHz);
+// the search takes the best.  Counted work: 2 flops x chains x reuse x iters
+// per thread; the grid is `blocks` x `threads`.  The accumulators' sum goes
+// to `sink` (caller-owned device memory, one double per thread), so nothing
+// is removed by the compiler.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,12 +21,20 @@
 
 namespace {
 
+// One fused multiply-add per step.  Spelled as a call, not as j * x + acc:
+// the product of loop-invariant operands could otherwise be hoisted out of
+// the loop, leaving additions to be timed.
+__device__ __forceinline__ double fma_op(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_op(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <typename T, int kChains, int kReuse>
-__global__ void __launch_bounds__(1024) k_fma(int iters, double* __restrict__ sink) {
+__global__ void __launch_bounds__(1024) k_fma(int iters, T m, double* __restrict__ sink) {
+  // operands from a run-time value: registers, like the sweeps' block entries
+  // (compile-time constants could be taken from the constant bank instead)
   T j[kChains], x[kReuse], acc[kChains][kReuse];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) {
-    j[k] = (T)(1.0 - 1e-3 * k);
+    j[k] = m - (T)(1e-3 * k);
 #pragma unroll
     for (int r = 0; r < kReuse; ++r) acc[k][r] = (T)0;
   }
@@ -34,7 +44,7 @@ __global__ void __launch_bounds__(1024) k_fma(int iters, double* __restrict__ si
 #pragma unroll
     for (int k = 0; k < kChains; ++k)
 #pragma unroll
-      for (int r = 0; r < kReuse; ++r) acc[k][r] = j[k] * x[r] + acc[k][r];  // contracts to one FMA
+      for (int r = 0; r < kReuse; ++r) acc[k][r] = fma_op(j[k], x[r], acc[k][r]);
   }
   T s = 0;
 #pragma unroll
@@ -46,9 +56,9 @@ __global__ void __launch_bounds__(1024) k_fma(int iters, double* __restrict__ si
 
 template <typename T, int kChains>
 cudaError_t launch_reuse(int reuse, int blocks, int threads, int iters, double* sink, cudaStream_t s) {
-  if (reuse == 1) k_fma<T, kChains, 1><<<blocks, threads, 0, s>>>(iters, sink);
-  else if (reuse == 2) k_fma<T, kChains, 2><<<blocks, threads, 0, s>>>(iters, sink);
-  else k_fma<T, kChains, 4><<<blocks, threads, 0, s>>>(iters, sink);
+  if (reuse == 1) k_fma<T, kChains, 1><<<blocks, threads, 0, s>>>(iters, (T)1, sink);
+  else if (reuse == 2) k_fma<T, kChains, 2><<<blocks, threads, 0, s>>>(iters, (T)1, sink);
+  else k_fma<T, kChains, 4><<<blocks, threads, 0, s>>>(iters, (T)1, sink);
   return cudaGetLastError();
 }
 
