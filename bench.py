@@ -539,16 +539,20 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
     p = inputs.config_problem("c3")
     n, b, N = p.mesh.n_nodes, p.block, p.n_harm
     dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-    flags = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
+    flags = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF
     J = fnlh.DeviceJacobian(dm, b, flags, dev)
     fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
     Bh = torch.from_numpy(p.b).pin_memory()
     Xh = torch.empty_like(Bh).pin_memory()
     B = Bh.to(dev)
     X = torch.zeros_like(B)
-    ws = fnlh.workspace(n, b, N, dev)
+    # the mixed solves' workspace holds the float-float shadows: their intermediate checks run on the FP32
+    # units, the certifying one in FP64 (fnlh_solve); the FP64 workspace (the largest) serves the FP64 solve
+    ws = fnlh.solve_workspace(n, b, N, flags, dev, fnlh.FNLH_F64)
+    ws_ff = {prec: fnlh.solve_workspace(n, b, N, flags, dev, prec) for prec in (fnlh.FNLH_F32, fnlh.FNLH_BF16)}
     out = {"workload": f"c3: 160x128x102 hex passage, {n} nodes, {p.mesh.n_edges} edges, b=6, mean + {N} "
-                       f"harmonics, CFL 20, to a {tol:g} relative FP64 residual per system, from zero",
+                       f"harmonics, CFL 20, to a {tol:g} relative FP64 residual per system, from zero; mixed "
+                       f"solves with float-float intermediate checks and an FP64 certifying check",
            "unit": "s", "higher_is_better": False}
     # inner sweeps per FP64 residual: the best of a scan of 10..40 on this workload (every run needs
     # ~60 sweeps; each extra check costs one FP64 residual)
@@ -556,10 +560,11 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
     zg = fnlh.FNLH_SOLVE_ZERO_GUESS
     sols = {}
     for name, prec, inner in cases:
-        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=ws, raise_on_error=False, flags=zg)  # warm
+        w = ws_ff.get(prec, ws)
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 2, ws=w, raise_on_error=False, flags=zg)  # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=ws,
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=w,
                                                   raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
@@ -568,7 +573,7 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         B.copy_(Bh, non_blocking=True)
-        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=ws, raise_on_error=False, flags=zg)
+        fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=w, raise_on_error=False, flags=zg)
         Xh.copy_(X, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
@@ -578,6 +583,16 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
                      "rel_residual_per_system": [float(v) for v in rel],
                      "e2e": {"seconds": e0.elapsed_time(e1) * 1e-3, "h2d_bytes": Bh.numel() * 8,
                              "d2h_bytes": Xh.numel() * 8}}
+    # the same mixed solves with every check in FP64 (the plain-size workspace has no float-float shadows)
+    for name, prec, inner in cases[1:]:
+        w = fnlh.workspace(n, b, N, dev, precision=prec)
+        t0 = time.perf_counter()
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=w,
+                                                  raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        out[name]["fp64_checks"] = {"seconds": time.perf_counter() - t0, "checks": checks, "sweeps": sweeps,
+                                    "status": fnlh.fnlh_strerror(st), "max_rel_residual": float(np.max(rel))}
+        del w
     if out["f64"]["status"] == "success":
         for name in ("f32", "bf16"):
             out[name]["speedup_vs_f64"] = out["f64"]["seconds"] / out[name]["seconds"]
@@ -591,7 +606,7 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
         out[name]["inner_sweep"] = {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
                                     "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                                     "frac_hbm_nominal_7900": alg / (ms * 1e-3) / 1e9 / 7900.0}
-    del dm, J, B, X, ws
+    del dm, J, B, X, ws, ws_ff
     torch.cuda.empty_cache()
     if with_oracle:
         import oracle

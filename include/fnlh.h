@@ -86,7 +86,12 @@ enum fnlh_prep_flags {
     /* a copy of col_idx whose top three bits tag each entry: the passage
      * offset of a periodic edge, and whether it crosses a partition; required
      * by every call on a mesh with `periodic` or `part` */
-    FNLH_PREP_TAGS = 8
+    FNLH_PREP_TAGS = 8,
+    /* float-float copies (each FP64 entry as an FP32 pair hi + lo, |entry - hi - lo| <= 2^-48 |entry|) of
+     * the off-diagonal blocks and of J_ii + D_i I in the original basis: with them, and the workspace of
+     * fnlh_solve_workspace_bytes, the intermediate residual checks of a mixed-precision fnlh_solve run on
+     * the FP32 units (see fnlh_solve) */
+    FNLH_PREP_FF = 16
 };
 
 #define FNLH_MAX_HARMONICS 64
@@ -244,6 +249,13 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
 #define FNLH_SOLVE_ZERO_GUESS 1     /* start from x0 = 0 (X is overwritten; the first residual is B) */
 #define FNLH_SOLVE_MASK_CONVERGED 2 /* systems already at tol are not swept again (their x is kept) */
 
+/* Workspace bytes of fnlh_solve: fnlh_workspace_bytes, plus for FNLH_F32 /
+ * FNLH_BF16 with FNLH_PREP_FF in prep_flags the float-float shadows of B and
+ * x ([n][C][b] FP32 pairs each) that its float-float checks read.  0 for an
+ * unsupported block size, harmonic count or precision. */
+size_t fnlh_solve_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision,
+                                  int32_t prep_flags);
+
 /* Solve every system to ||r_k|| <= tol ||B_k||.  With x0 = 0 and tol = 1e-2 this is
  * the paper's linear-solve rule (Results, Table fnlh_para: the residual drops
  * two orders of magnitude from its initial value; max_checks and inner_sweeps
@@ -252,11 +264,22 @@ int fnlh_residual(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_harm,
  * FNLH_F32 / FNLH_BF16: defect correction -- FP64 residual r = B - A x,
  * `inner_sweeps` sweeps on A e = r with the low-precision blocks and FP32
  * arithmetic from e = 0 (r and e rotated in FP32), then x += e with the sum in
- * FP64; repeated.  On a mesh with `part` the FP64 solve is a defect
+ * FP64; repeated.  Float-float checks: when J's prep blob holds FNLH_PREP_FF
+ * and the workspace has fnlh_solve_workspace_bytes, every check of a mixed
+ * solve after the first evaluates B - A x in float-float arithmetic on the
+ * FP32 units (about 44 bits: its norms agree with the FP64 residual's to
+ * ~1e-5 relative at a 1e-8 residual) -- except that a check is always made,
+ * or confirmed, with the FP64 residual before the solve reports convergence:
+ * a float-float check at tol is followed at once by an FP64 one, and when the
+ * residual's decay (the last two checks' ratio) predicts the next check at
+ * or below 2 tol, the next check is FP64 directly.  Meshes with `periodic`
+ * keep FP64 checks.
+ * On a mesh with `part` the FP64 solve is a defect
  * correction too (inner FP64 sweeps without the cross-partition couplings,
  * FP64 residual with them).  X: in x0 (ignored with FNLH_SOLVE_ZERO_GUESS), out x.
  * SYNCHRONISING (reads the norms after every check).  Outputs (host, each
- * nullable): *checks_done residual evaluations, *sweeps_done total sweeps,
+ * nullable): *checks_done residual checks (a float-float check and the FP64
+ * residual that confirms it count as one), *sweeps_done total sweeps,
  * rel_res [K] final ||r_k||/||B_k||.  Returns FNLH_ERR_NOT_CONVERGED after
  * max_checks checks above tol, FNLH_ERR_NONFINITE / FNLH_ERR_DIVERGED on a
  * non-finite or growing (x1e3) residual. */

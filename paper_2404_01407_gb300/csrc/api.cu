@@ -15,7 +15,7 @@ int prepare_impl(const fnlh_mesh*, fnlh_jacobian*, cudaStream_t);
 int relax_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, const double*, double*,
                int, int, void*, cudaStream_t);
 int solve_impl(const fnlh_mesh*, const fnlh_jacobian*, int, const double*, const double*, const double*, double*, int,
-               double, int, int, int, void*, int*, int*, double*, cudaStream_t);
+               double, int, int, int, void*, size_t, int*, int*, double*, cudaStream_t);
 int residual_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*, double*,
                     float*, const float*, int, double*, void*, cudaStream_t);
 Systems make_systems(int n_harm, const double* omega, const double* sigma);
@@ -172,6 +172,13 @@ size_t fnlh_prep_bytes(int32_t n_nodes, int32_t nnz, int32_t block, int32_t prep
   return prep_layout(n_nodes, nnz, block, prep_flags).total;
 }
 
+size_t fnlh_solve_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision,
+                                  int32_t prep_flags) {
+  const size_t base = fnlh_workspace_bytes(n_nodes, block, n_harm, precision);
+  if (base == 0 || precision == FNLH_F64 || !(prep_flags & FNLH_PREP_FF)) return base;
+  return ws_layout(n_nodes, block, n_harm, precision).total_ff;
+}
+
 size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int32_t precision) {
   if (n_nodes < 0 || (block != 5 && block != 6) || n_harm < 0 || n_harm > FNLH_MAX_HARMONICS) return 0;
   if (!valid_precision(precision)) return 0;
@@ -198,7 +205,8 @@ int fnlh_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, fnlh_stream_t stream) 
   FNLH_TRY(check_jac(mesh, J));
   if (!J->prep) return FNLH_ERR_WORKSPACE;
   if (!aligned(J->prep, 256)) return FNLH_ERR_ARG;
-  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16 | FNLH_PREP_TAGS)) return FNLH_ERR_ARG;
+  if (J->prep_flags & ~(FNLH_PREP_F64 | FNLH_PREP_F32 | FNLH_PREP_BF16 | FNLH_PREP_TAGS | FNLH_PREP_FF))
+    return FNLH_ERR_ARG;
   if (J->prep_bytes < fnlh_prep_bytes(J->n_nodes, J->nnz, J->block, J->prep_flags)) return FNLH_ERR_WORKSPACE;
   if (tagged_mesh(mesh) && !(J->prep_flags & FNLH_PREP_TAGS)) return FNLH_ERR_WORKSPACE;
   if (mesh->periodic) FNLH_TRY(check_mesh(mesh, true));  // passage tags come from csr_edge and edge_nodes
@@ -253,7 +261,7 @@ int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
   FNLH_TRY(check_ws(workspace, workspace_bytes, mesh->n_nodes, J->block, n_harm, precision));
   FNLH_TRY(check_pairs(mesh->n_nodes, n_harm));
   return solve_impl(mesh, J, n_harm, omega, sigma, B, X, precision, tol, inner_sweeps, max_checks, flags, workspace,
-                    checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
+                    workspace_bytes, checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
 }
 
 size_t fnlh_batched_extra_bytes(int32_t n_rows) { return n_rows > 0 ? batched_extra_bytes(n_rows) : 0; }

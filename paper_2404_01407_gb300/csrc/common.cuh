@@ -278,6 +278,45 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
   }
 }
 
+// --------------------------------------------------------- float-float
+//
+// A value as an unevaluated sum of two FP32 numbers, hi + lo with |lo| <=
+// ulp(hi) / 2 (Dekker 1971): products and sums below are exact up to
+// O(2^-44) of the magnitudes involved.  Every operation is spelled with an
+// explicit rounding intrinsic so that the compiler neither fuses nor
+// reassociates it.
+
+// FP64 -> (hi, lo): hi the nearest FP32, lo the nearest FP32 to the rest.
+__device__ __forceinline__ float2 ff_split(double d) {
+  const float h = __double2float_rn(d);
+  return make_float2(h, __double2float_rn(d - (double)h));
+}
+
+// (h, l) -= a * b for float-float a and b: the product of the high parts
+// exactly (TwoProduct with one FMA), the cross terms in FP32, and the
+// subtraction from the high part exactly (TwoSum, 6 additions).
+__device__ __forceinline__ void ff_sub_prod(float& h, float& l, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float pe = __fmaf_rn(a.x, b.x, -p);                            // a.x b.x - p, exact
+  const float pl = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe));       // the rest of the product
+  const float t = __fsub_rn(h, p);
+  const float z = __fsub_rn(t, h);
+  const float e = __fsub_rn(__fsub_rn(h, __fsub_rn(t, z)), __fadd_rn(p, z));  // (h - p) - t, exact
+  h = t;
+  l = __fadd_rn(l, __fsub_rn(e, pl));
+}
+
+// (h, l) += e for an FP32 e: exact sum of the high parts (TwoSum), then
+// renormalised so that |l| stays below half an ulp of h.
+__device__ __forceinline__ float2 ff_add_f(float2 a, float e) {
+  const float t = __fadd_rn(a.x, e);
+  const float z = __fsub_rn(t, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, z)), __fsub_rn(e, z));
+  const float l = __fadd_rn(a.y, err);
+  const float h = __fadd_rn(t, l);
+  return make_float2(h, __fsub_rn(l, __fsub_rn(h, t)));
+}
+
 // ---------------------------------------------------------- workspace map
 //
 // [0, 256)                      status words (int32)
@@ -287,6 +326,8 @@ __device__ __forceinline__ void hess_solve(const TH* __restrict__ H, T s, T (&yr
 // pivinv                        FP64 only: [n][K][b] pairs (d, s) / (d^2 + s^2) of the shifted triangular solves
 struct WsLayout {
   size_t status, partials, norms, vec[3], pivinv, total, vec_bytes;
+  // fnlh_solve's float-float shadows after `total` ([n][C][b] float2 each, FP32 / BF16 only):
+  size_t bff, xff, total_ff;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -310,6 +351,15 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
     off = align256(off + (size_t)n * K * block * 2 * sizeof(double));
   }
   w.total = off;
+  w.bff = w.xff = (size_t)-1;
+  if (precision != FNLH_F64) {
+    const size_t shadow = (size_t)n * (2 * K - 1) * block * 2 * sizeof(float);
+    w.bff = off;
+    off = align256(off + shadow);
+    w.xff = off;
+    off = align256(off + shadow);
+  }
+  w.total_ff = off;
   return w;
 }
 
@@ -323,8 +373,10 @@ inline WsLayout ws_layout(int32_t n, int32_t block, int32_t n_harm, int32_t prec
 // cols  [nnz] int32     col_idx with the passage and partition tags (FNLH_PREP_TAGS)
 // info  int32 words: [0] nonzero when the blocks do NOT have the frozen-
 //       turbulence zero pattern (see k_check_structure)
+// offdff [nnz][b][b] float2, diagff [n][b][b] float2 (FNLH_PREP_FF): the
+//       original-basis J_ij and J_ii + D_i I as float-float pairs (hi, lo)
 struct PrepLayout {
-  size_t info, rot, hess, hessf, rotf, offd64, offd32, offd16, cols, total;
+  size_t info, rot, hess, hessf, rotf, offd64, offd32, offd16, cols, offdff, diagff, total;
 };
 
 inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) {
@@ -359,6 +411,13 @@ inline PrepLayout prep_layout(int32_t n, int32_t nnz, int32_t b, int32_t flags) 
   if (flags & FNLH_PREP_TAGS) {
     p.cols = off;
     off = align256(off + (size_t)nnz * 4);
+  }
+  p.offdff = p.diagff = (size_t)-1;
+  if (flags & FNLH_PREP_FF) {
+    p.offdff = off;
+    off = align256(off + (size_t)nnz * bb * 8);
+    p.diagff = off;
+    off = align256(off + (size_t)n * bb * 8);
   }
   p.total = off;
   return p;

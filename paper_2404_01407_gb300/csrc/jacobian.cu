@@ -425,6 +425,23 @@ int launch_build(const BuildArgs& a, cudaStream_t s) {
   return FNLH_OK;
 }
 
+// Float-float copies for the mixed solve's float-float residual checks: the
+// off-diagonal blocks, and the diagonal blocks with the pseudo-time term
+// folded in (J_ii + D_i I, summed in FP64 before the split).
+template <int BS>
+__global__ void __launch_bounds__(256) k_split_ff(long long n_offd, long long n_diag, const double* __restrict__ offd,
+                                                  const double* __restrict__ diag, const double* __restrict__ D,
+                                                  float2* __restrict__ offdff, float2* __restrict__ diagff) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_offd) offdff[e] = ff_split(offd[e]);
+  if (e < n_diag) {
+    const long long i = e / (BS * BS);
+    const int rc = (int)(e - i * BS * BS);
+    const double v = diag[e] + ((rc / BS == rc % BS) ? D[i] : 0.0);
+    diagff[e] = ff_split(v);
+  }
+}
+
 template <int BS>
 int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
   const PrepLayout L = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
@@ -451,6 +468,16 @@ int launch_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, cudaStream_t s) {
     k_rotate_offd<BS><<<(J->nnz + 127) / 128, 128, 0, s>>>(n, J->nnz, mesh->row_ptr, mesh->col_idx, J->offd, rot,
                                                          o64, o32, o16);
     FNLH_LAUNCH_CHECK();
+  }
+  if (L.offdff != (size_t)-1) {
+    const long long no = (long long)J->nnz * BS * BS, nd = (long long)n * BS * BS;
+    const long long cnt = std::max(no, nd);
+    if (cnt > 0) {
+      k_split_ff<BS><<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(no, nd, J->offd, J->diag, J->D,
+                                                                  at<float2>(J->prep, L.offdff),
+                                                                  at<float2>(J->prep, L.diagff));
+      FNLH_LAUNCH_CHECK();
+    }
   }
   if (L.cols != (size_t)-1 && n > 0) {
     k_tag_columns<<<(n + 127) / 128, 128, 0, s>>>(n, mesh->row_ptr, mesh->col_idx, mesh->csr_edge, mesh->edge_nodes,

@@ -34,6 +34,12 @@ struct ResArgs {
   int32_t x_zero;     // x is zero: r = B without reading X
   double* partials; // [gridDim][2K]
   Systems sys;
+  // float-float form (k_residual_ff): the prep blob's copies and the solve's shadows
+  const float2* offdff;  // [nnz][b][b]
+  const float2* diagff;  // [n][b][b], J_ii + D_i I
+  const float2* bff;     // [n][C][b]
+  const float2* xff;     // [n][C][b]
+  float2 omega_ff[kMaxSys];  // omega_k as a float-float pair
 };
 
 // r for one (node, system) pair; returns ||r||^2 and ||B||^2 contributions.
@@ -230,6 +236,145 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_cons
   for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) a.partials[(size_t)blockIdx.x * 2 * K + t] = s_acc[t];
 }
 
+// Float-float residual of the mixed solve's checks, on the FP32 units: B, x,
+// the blocks and J_ii + D_i I as FP32 pairs (hi + lo), each multiply-add of
+// the FP64 form as one exact product of the high parts, FP32 cross terms and
+// one exact subtraction (ff_sub_prod) -- about 44 bits, so a residual at 1e-8
+// of ||B|| keeps ~5 significant digits.  Mapping: a warp takes kFfNodes
+// nodes and a lane one row q of one node (30 lanes busy), so that a block's
+// rows are read by consecutive lanes and each row, held in registers, serves
+// up to kFfSys systems; the rotation Q_i^T r to the sweeps' basis gathers the
+// node's rows with shuffles.  Writes Q_i^T r (FP32) like the FP64 kernel, and
+// per block the sums ||r_k||^2 and ||B_k||^2 (from B's high parts) in a
+// fixed order.  Not for meshes with periodic edges (no phase factors here).
+constexpr int kFfSys = 4;
+
+template <int BS>
+__global__ void __launch_bounds__(kResidualThreads) k_residual_ff(const __grid_constant__ ResArgs a) {
+  constexpr int kNodes = 30 / BS;  // nodes per warp: 5 for b = 6, 6 for b = 5
+  constexpr int kWarps = kResidualThreads / 32;
+  __shared__ double s_acc[kWarps][2 * kMaxSys];
+  const int K = a.sys.K, C = a.sys.C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u = lane / BS, q = lane - u * BS;
+  const bool live = lane < kNodes * BS;
+  for (int t = lane; t < 2 * K; t += 32) s_acc[warp][t] = 0.0;
+  __syncwarp();
+  bool pattern = false;
+  if constexpr (BS == 6) pattern = a.info != nullptr && __ldg(a.info) == 0;
+  const int groups = (a.n + kNodes - 1) / kNodes;
+  for (int grp = blockIdx.x * kWarps + warp; grp < groups; grp += gridDim.x * kWarps) {
+    const int i = grp * kNodes + u;
+    const bool valid = live && i < a.n;
+    const int p0 = valid ? a.row_ptr[i] : 0, p1 = valid ? a.row_ptr[i + 1] : 0;
+    const float2 vff = valid ? ff_split(a.vol[i]) : make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < K; k0 += kFfSys) {
+      float rh[kFfSys], rl[kFfSys], ih[kFfSys], il[kFfSys];
+      float bsq[kFfSys];
+#pragma unroll
+      for (int s = 0; s < kFfSys; ++s) {
+        const int k = k0 + s;
+        float2 br = make_float2(0.f, 0.f), bi = br;
+        if (valid && k < K) {
+          const int c0 = (k == 0) ? 0 : 2 * k - 1;
+          br = a.bff[((size_t)i * C + c0) * BS + q];
+          if (k > 0) bi = a.bff[((size_t)i * C + c0 + 1) * BS + q];
+        }
+        rh[s] = br.x;
+        rl[s] = br.y;
+        ih[s] = bi.x;
+        il[s] = bi.y;
+        bsq[s] = br.x * br.x + bi.x * bi.x;
+      }
+      // off-diagonal blocks: row q of J_ij times x_j for the pass's systems
+      for (int p = p0; p < p1; ++p) {
+        const int j = col_of(a.col_idx[p]);
+        float2 jr[BS];
+#pragma unroll
+        for (int t = 0; t < BS; ++t) jr[t] = a.offdff[((size_t)p * BS + q) * BS + t];
+        const bool skip_last = pattern && q < BS - 1;  // frozen turbulence: structural zero
+#pragma unroll
+        for (int s = 0; s < kFfSys; ++s) {
+          const int k = k0 + s;
+          if (k >= K) break;
+          const int c0 = (k == 0) ? 0 : 2 * k - 1;
+          const float2* xr = a.xff + ((size_t)j * C + c0) * BS;
+#pragma unroll
+          for (int t = 0; t < BS; ++t) {
+            if (t == BS - 1 && skip_last) continue;
+            ff_sub_prod(rh[s], rl[s], jr[t], xr[t]);
+            if (k > 0) ff_sub_prod(ih[s], il[s], jr[t], xr[BS + t]);
+          }
+        }
+      }
+      // diagonal block (J_ii + D_i I) and the spectral term i omega_k V_i, then the outputs
+      float2 pr[BS], qc[BS];
+#pragma unroll
+      for (int t = 0; t < BS; ++t) {
+        pr[t] = valid ? a.diagff[((size_t)i * BS + q) * BS + t] : make_float2(0.f, 0.f);
+        qc[t] = make_float2(valid ? __ldg(a.rotf + (size_t)i * BS * BS + t * BS + q) : 0.f, 0.f);  // Q[t][q]
+      }
+#pragma unroll
+      for (int s = 0; s < kFfSys; ++s) {
+        const int k = k0 + s;
+        if (k >= K) break;  // uniform over the warp
+        const int c0 = (k == 0) ? 0 : 2 * k - 1;
+        if (valid) {
+          const float2* xi = a.xff + ((size_t)i * C + c0) * BS;
+#pragma unroll
+          for (int t = 0; t < BS; ++t) {
+            ff_sub_prod(rh[s], rl[s], pr[t], xi[t]);
+            if (k > 0) ff_sub_prod(ih[s], il[s], pr[t], xi[BS + t]);
+          }
+          if (k > 0) {
+            // r -= i w x: re += w x_im, im -= w x_re; w = omega_k V_i as a float-float product
+            const float2 om = a.omega_ff[k];
+            const float wp = __fmul_rn(om.x, vff.x);
+            const float we = __fmaf_rn(om.x, vff.y, __fmaf_rn(om.y, vff.x, __fmaf_rn(om.x, vff.x, -wp)));
+            ff_sub_prod(rh[s], rl[s], make_float2(-wp, -we), xi[BS + q]);
+            ff_sub_prod(ih[s], il[s], make_float2(wp, we), xi[q]);
+          }
+        }
+        const float r_re = valid ? __fadd_rn(rh[s], rl[s]) : 0.f;
+        const float r_im = (valid && k > 0) ? __fadd_rn(ih[s], il[s]) : 0.f;
+        // squares summed in FP32 over the warp (the checks need a few digits), added to
+        // the block's FP64 sums once per warp and pass
+        float rs = r_re * r_re + r_im * r_im;
+        float bs = bsq[s];
+        // Q_i^T r, row q: sum over the node's rows t, gathered from lanes u BS + t
+        float o_re = 0.f, o_im = 0.f;
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+          const int src = min(u * BS + t, 31);
+          const float vr = __shfl_sync(0xffffffffu, r_re, src);
+          const float vi = __shfl_sync(0xffffffffu, r_im, src);
+          o_re += qc[t].x * vr;
+          o_im += qc[t].x * vi;
+        }
+        if (valid) {
+          float* rp = a.r32rot + ((size_t)i * K + k) * 2 * BS;
+          rp[2 * q] = o_re;
+          rp[2 * q + 1] = (k > 0) ? o_im : 0.0f;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          rs += __shfl_xor_sync(0xffffffffu, rs, off);
+          bs += __shfl_xor_sync(0xffffffffu, bs, off);
+        }
+        if (lane == 0) {
+          s_acc[warp][2 * k] += (double)rs;
+          s_acc[warp][2 * k + 1] += (double)bs;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kWarps; ++w) v += s_acc[w][t];
+    a.partials[(size_t)blockIdx.x * 2 * K + t] = v;
+  }
+}
 // norms[t] = sum over blocks of partials[blk][t], in block order.
 __global__ void k_reduce_partials(const double* __restrict__ partials, int nblk, int width, double* __restrict__ norms) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,7 +394,7 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
                     const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
                     cudaStream_t s) {
   const WsLayout W = ws_layout(J->n_nodes, J->block, sys.K - 1, FNLH_F64);
-  ResArgs a;
+  ResArgs a{};
   a.n = J->n_nodes;
   a.row_ptr = m->row_ptr;
   a.col_idx = csr_columns(m, J);
@@ -270,6 +415,48 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
   const int threads = kResidualThreads;
   if (J->block == 5) k_residual<5><<<grid, threads, 0, s>>>(a);
   else k_residual<6><<<grid, threads, 0, s>>>(a);
+  FNLH_LAUNCH_CHECK();
+  k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(a.partials, grid, 2 * sys.K, norms);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
+// The float-float residual of a mixed solve's check: Q^T r in FP32 into
+// r32rot, ||r_k||^2 (and ||B_k||^2 from B's high parts) into norms.  bff, xff:
+// the solve's shadows of B and x; the prep blob must hold FNLH_PREP_FF.
+int residual_ff_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const float2* bff,
+                       const float2* xff, float* r32rot, const float* rotf, double* norms, void* ws, cudaStream_t s) {
+  const WsLayout W = ws_layout(J->n_nodes, J->block, sys.K - 1, FNLH_F64);
+  const PrepLayout L = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+  if (L.offdff == (size_t)-1) return FNLH_ERR_WORKSPACE;
+  ResArgs a{};
+  a.n = J->n_nodes;
+  a.row_ptr = m->row_ptr;
+  a.col_idx = csr_columns(m, J);
+  a.offd = nullptr;
+  a.diag = nullptr;
+  a.D = nullptr;
+  a.vol = m->vol;
+  a.B = nullptr;
+  a.X = nullptr;
+  a.r = nullptr;
+  a.r32rot = r32rot;
+  a.rotf = rotf;
+  a.info = prep_info(J);
+  a.x_zero = 0;
+  a.partials = at<double>(ws, W.partials);
+  a.sys = sys;
+  a.offdff = at<float2>(J->prep, L.offdff);
+  a.diagff = at<float2>(J->prep, L.diagff);
+  a.bff = bff;
+  a.xff = xff;
+  for (int k = 0; k < kMaxSys; ++k) {
+    const float h = (float)sys.omega[k];
+    a.omega_ff[k] = make_float2(h, (float)(sys.omega[k] - (double)h));
+  }
+  const int grid = residual_grid(a.n);
+  if (J->block == 5) k_residual_ff<5><<<grid, kResidualThreads, 0, s>>>(a);
+  else k_residual_ff<6><<<grid, kResidualThreads, 0, s>>>(a);
   FNLH_LAUNCH_CHECK();
   k_reduce_partials<<<1, 2 * kMaxSys, 0, s>>>(a.partials, grid, 2 * sys.K, norms);
   FNLH_LAUNCH_CHECK();
@@ -310,7 +497,7 @@ int residual_noalloc_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Sy
   double* partials = nullptr;
   const int rc = scratch_address(&partials);
   if (rc) return rc;
-  ResArgs a;
+  ResArgs a{};
   a.n = J->n_nodes;
   a.row_ptr = m->row_ptr;
   a.col_idx = csr_columns(m, J);

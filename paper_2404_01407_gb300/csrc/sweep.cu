@@ -136,9 +136,12 @@ __global__ void __launch_bounds__(256) k_rotate_out(long long count, int K, cons
 
 // x_i[c] += Q_i y_i[c] with the product in FP32 and the sum in FP64: the
 // defect-correction update, whose correction only needs FP32 accuracy.
+// xff (nullable): the float-float shadow of x, advanced by the same FP32
+// correction in float-float arithmetic (no FP64 conversion per value).
 template <int BS>
 __global__ void __launch_bounds__(256) k_update_f32(long long count, int K, const float* __restrict__ rotf,
-                                                    const float* __restrict__ y, double* __restrict__ x) {
+                                                    const float* __restrict__ y, double* __restrict__ x,
+                                                    float2* __restrict__ xff = nullptr) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= count) return;
   const long long i = g / K;
@@ -152,7 +155,20 @@ __global__ void __launch_bounds__(256) k_update_f32(long long count, int K, cons
     vr[t] = in[2 * t];
     vi[t] = in[2 * t + 1];
   }
-  double* xr = x + (i * C + (k == 0 ? 0 : 2 * k - 1)) * BS;
+  // All loads of the read-modify-write are issued before any store, so one
+  // memory round trip covers the whole update of this (node, system).
+  const long long row0 = i * C + (k == 0 ? 0 : 2 * k - 1);
+  double* xr = x + row0 * BS;
+  const int nrow = k == 0 ? BS : 2 * BS;
+  double xo[2 * BS];
+  float2 fo[2 * BS];
+#pragma unroll
+  for (int t = 0; t < 2 * BS; ++t) {
+    if (t < nrow) {
+      xo[t] = xr[t];
+      if (xff) fo[t] = xff[row0 * BS + t];
+    }
+  }
 #pragma unroll
   for (int r = 0; r < BS; ++r) {
     float ar = 0.0f, ai = 0.0f;
@@ -162,9 +178,20 @@ __global__ void __launch_bounds__(256) k_update_f32(long long count, int K, cons
       ar += q * vr[t];
       ai += q * vi[t];
     }
-    xr[r] += (double)ar;
-    if (k > 0) xr[BS + r] += (double)ai;
+    xr[r] = xo[r] + (double)ar;
+    if (xff) xff[row0 * BS + r] = ff_add_f(fo[r], ar);
+    if (k > 0) {
+      xr[BS + r] = xo[BS + r] + (double)ai;
+      if (xff) xff[row0 * BS + BS + r] = ff_add_f(fo[BS + r], ai);
+    }
   }
+}
+
+// v -> (hi, lo) FP32 pairs: the float-float shadows of B and x.
+__global__ void __launch_bounds__(256) k_split_vec(long long count, const double* __restrict__ v,
+                                                   float2* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = ff_split(v[e]);
 }
 
 static inline unsigned blocks_for(long long count, int threads) {
@@ -434,6 +461,8 @@ int relax_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const dou
 int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const double* B,
                     const double* X, double* r, float* r32rot, const float* rotf, int x_zero, double* norms, void* ws,
                     cudaStream_t s);
+int residual_ff_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const float2* bff,
+                       const float2* xff, float* r32rot, const float* rotf, double* norms, void* ws, cudaStream_t s);
 
 struct Check {
   double rel[kMaxSys];
@@ -460,7 +489,7 @@ static int check_norms(const double* hn, int K, double tol, Check* ck, bool firs
 template <int BS, typename TJ, typename T>
 int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
                 const double* B, double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
-                int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
+                size_t ws_bytes, int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
   SweepOperands op;
   int rc = sweep_operands(m, J, precision, &op);
   if (rc) return rc;
@@ -495,17 +524,62 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
     pivinv = at<double>(ws, W.pivinv);
     if ((rc = pivot_inverses<BS>(m, (const double*)op.hess, sys, pivinv, s))) return rc;
   }
-  for (;;) {
-    // mixed: Q^T r in FP32 straight into v0; FP64 defect correction: r into v2
-    double* r64 = (defect && !mixed) ? (double*)v2 : nullptr;
-    rc = residual_launch(m, J, sys, B, X, r64, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms, ws, s);
-    x_zero = false;
-    if (rc) return rc;
+  // Float-float checks (mixed solves whose prep blob has FNLH_PREP_FF and whose
+  // workspace holds the shadows): every check after the first evaluates B - A x
+  // on the FP32 units from float-float shadows of B and x (x's is rewritten
+  // by every update); a passing one is confirmed at once by the FP64 residual,
+  // and a check that the residual's decay predicts at or below 2 tol is made
+  // in FP64 directly, so that convergence is always certified in FP64.
+  const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
+  const bool ff = mixed && n > 0 && PL.offdff != (size_t)-1 && m->periodic == nullptr && ws_bytes >= W.total_ff;
+  float2* bff = ff ? at<float2>(ws, W.bff) : nullptr;
+  float2* xff = ff ? at<float2>(ws, W.xff) : nullptr;
+  if (ff) {
+    const long long nv = (long long)n * sys.C * BS;
+    k_split_vec<<<blocks_for(nv, 256), 256, 0, s>>>(nv, B, bff);
+    FNLH_LAUNCH_CHECK();
+    if (x_zero) {
+      FNLH_CUDA_TRY(cudaMemsetAsync(xff, 0, sizeof(float2) * (size_t)nv, s));
+    } else {
+      k_split_vec<<<blocks_for(nv, 256), 256, 0, s>>>(nv, X, xff);
+      FNLH_LAUNCH_CHECK();
+    }
+  }
+  double bnorm[kMaxSys];  // ||B_k||^2 from the first (FP64) check
+  double prev_worst = -1.0;
+  bool fp64_next = false;
+  auto fetch = [&]() -> int {
     FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
     FNLH_CUDA_TRY(cudaStreamSynchronize(s));
-    rc = check_norms(hn, K, tol, &ck, checks == 0, &conv);
+    return FNLH_OK;
+  };
+  for (;;) {
+    const bool use_ff = ff && checks > 0 && !fp64_next;
+    if (use_ff) {
+      rc = residual_ff_launch(m, J, sys, bff, xff, (float*)v0, op.rotf, norms, ws, s);
+      if (rc || (rc = fetch())) return rc;
+      for (int k = 0; k < K; ++k) hn[2 * k + 1] = bnorm[k];
+      rc = check_norms(hn, K, tol, &ck, false, &conv);
+    }
+    if (!use_ff || (rc == FNLH_OK && conv)) {
+      // mixed: Q^T r in FP32 straight into v0; FP64 defect correction: r into v2
+      double* r64 = (defect && !mixed) ? (double*)v2 : nullptr;
+      rc = residual_launch(m, J, sys, B, X, r64, mixed ? (float*)v0 : nullptr, op.rotf, x_zero ? 1 : 0, norms, ws,
+                           s);
+      x_zero = false;
+      if (rc || (rc = fetch())) return rc;
+      if (checks == 0)
+        for (int k = 0; k < K; ++k) bnorm[k] = hn[2 * k + 1];
+      rc = check_norms(hn, K, tol, &ck, checks == 0, &conv);
+    }
     ++checks;
     if (rc || conv || checks >= max_checks) break;
+    if (ff) {  // does the decay predict the next check at or below 2 tol?  Then make it in FP64.
+      double worst = 0.0;
+      for (int k = 0; k < K; ++k) worst = fmax(worst, ck.rel[k]);
+      fp64_next = prev_worst > 0.0 && worst * worst / prev_worst <= 2.0 * tol;
+      prev_worst = worst;
+    }
     if (masking)  // converged systems are frozen for the following sweeps
       for (int k = 0; k < K; ++k)
         if (ck.rel[k] <= tol) active[k >> 6] &= ~(1ull << (k & 63));
@@ -520,7 +594,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
       const long long count = (long long)n * K;
       if constexpr (sizeof(T) == 4) {
         if (count > 0) {
-          k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X);
+          k_update_f32<BS><<<blocks_for(count, 256), 256, 0, s>>>(count, K, op.rotf, (const float*)res, X, xff);
           FNLH_LAUNCH_CHECK();
         }
       } else {
@@ -544,10 +618,10 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
 
 int solve_impl(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const double* omega, const double* sigma,
                const double* B, double* X, int precision, double tol, int inner, int max_checks, int flags, void* ws,
-               int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
+               size_t ws_bytes, int* checks_done, int* sweeps_done, double* rel_res, cudaStream_t s) {
 #define FNLH_SOLVE(BS, TJ, T)                                                                                   \
   solve_typed<BS, TJ, T>(m, J, n_harm, omega, sigma, B, X, precision, tol, inner, max_checks, flags, ws,       \
-                         checks_done, sweeps_done, rel_res, s)
+                         ws_bytes, checks_done, sweeps_done, rel_res, s)
   if (J->block == 5) {
     if (precision == FNLH_F64) return FNLH_SOLVE(5, double, double);
     if (precision == FNLH_F32) return FNLH_SOLVE(5, float, float);

@@ -36,7 +36,7 @@ FNLH_ERR_NOT_CONVERGED = -8
 FNLH_ERR_BAD_MESH = -9
 
 FNLH_F64, FNLH_F32, FNLH_BF16 = 0, 1, 2
-FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16, FNLH_PREP_TAGS = 1, 2, 4, 8
+FNLH_PREP_F64, FNLH_PREP_F32, FNLH_PREP_BF16, FNLH_PREP_TAGS, FNLH_PREP_FF = 1, 2, 4, 8, 16
 PRECISIONS = {"f64": FNLH_F64, "f32": FNLH_F32, "bf16": FNLH_BF16}
 PREP_FOR = {FNLH_F64: FNLH_PREP_F64, FNLH_F32: FNLH_PREP_F32, FNLH_BF16: FNLH_PREP_BF16}
 MAX_HARMONICS = 64
@@ -93,6 +93,7 @@ _SIGS = {
     "fnlh_mesh_build_csr": (ctypes.c_int, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "fnlh_prep_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
     "fnlh_workspace_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32]),
+    "fnlh_solve_workspace_bytes": (c_sz, [c_i32, c_i32, c_i32, c_i32, c_i32]),
     "fnlh_build_jacobian": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), c_vp, ctypes.POINTER(fnlh_params),
                                            ctypes.POINTER(fnlh_jacobian), c_vp]),
     "fnlh_prepare": (ctypes.c_int, [ctypes.POINTER(fnlh_mesh), ctypes.POINTER(fnlh_jacobian), c_vp]),
@@ -264,6 +265,13 @@ def workspace(n_nodes, block, n_harm, device="cuda", precision=FNLH_F64):
     return torch.empty((nbytes,), dtype=torch.uint8, device=device)
 
 
+def solve_workspace(n_nodes, block, n_harm, prep_flags, device="cuda", precision=FNLH_F64):
+    """Workspace for fnlh_solve, with room for the float-float checks when
+    prep_flags holds FNLH_PREP_FF and the precision is mixed."""
+    nbytes = fnlh_solve_workspace_bytes(n_nodes, block, n_harm, precision, prep_flags)
+    return torch.empty((nbytes,), dtype=torch.uint8, device=device)
+
+
 # ------------------------------------------------------- C entry points
 
 def fnlh_version() -> int:
@@ -287,6 +295,10 @@ def fnlh_prep_bytes(n_nodes, nnz, block, prep_flags) -> int:
 
 def fnlh_workspace_bytes(n_nodes, block, n_harm, precision=FNLH_F64) -> int:
     return int(lib().fnlh_workspace_bytes(n_nodes, block, n_harm, precision))
+
+
+def fnlh_solve_workspace_bytes(n_nodes, block, n_harm, precision, prep_flags) -> int:
+    return int(lib().fnlh_solve_workspace_bytes(n_nodes, block, n_harm, precision, prep_flags))
 
 
 def fnlh_build_jacobian(dmesh: DeviceMesh, Q: torch.Tensor, params: fnlh_params, J: DeviceJacobian, stream=None):
@@ -337,7 +349,7 @@ def fnlh_solve(dmesh, J, omega, B, X, precision, tol, inner_sweeps, max_checks, 
     n_harm = len(np.atleast_1d(omega))
     sg, sgp = _sigma(sigma, n_harm)
     if ws is None:
-        ws = workspace(dmesh.n_nodes, J.block, n_harm, B.device)
+        ws = solve_workspace(dmesh.n_nodes, J.block, n_harm, J.c.prep_flags, B.device, precision)
     checks, sweeps = c_i32(0), c_i32(0)
     rel = (c_f64 * (1 + n_harm))()
     st = lib().fnlh_solve(ctypes.byref(dmesh.c), ctypes.byref(J.c), n_harm, omp, sgp, _ptr(B), _ptr(X), int(precision),

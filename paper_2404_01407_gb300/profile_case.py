@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=1)
     ap.add_argument("--warm", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--ff", action="store_true", help="--op solve: float-float checks (FNLH_PREP_FF, solve workspace)")
     ap.add_argument("--rows", nargs="+", default=["60,40,40,2", "75,56,60,8", "94,82,60,4"],
                     help="--op batched: blade rows as nx,ny,nz,harmonics (row r: omega base 1 + 0.65 r)")
     ap.add_argument("--threads", type=int, default=0, help="--op batched: fnlh_tuning.threads (0: default)")
@@ -41,13 +42,16 @@ def main():
     p = inputs.problem(tuple(a.dims), a.block, a.harm, a.cfl, name="profile")
     dev = torch.device("cuda")
     dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-    J = fnlh.DeviceJacobian(dm, a.block, fnlh.PREP_FOR.get(prec, fnlh.FNLH_PREP_F64), dev)
+    prep = fnlh.PREP_FOR.get(prec, fnlh.FNLH_PREP_F64) | (fnlh.FNLH_PREP_FF if a.ff else 0)
+    J = fnlh.DeviceJacobian(dm, a.block, prep, dev)
     Q = torch.from_numpy(p.q).to(dev)
     params = fnlh.make_params(p.cfl)
     fnlh.fnlh_build_jacobian(dm, Q, params, J)
     B = torch.from_numpy(p.b).to(dev)
     X = torch.zeros_like(B)
     ws = fnlh.workspace(p.mesh.n_nodes, a.block, a.harm, dev)
+    if a.ff:
+        ws = fnlh.solve_workspace(p.mesh.n_nodes, a.block, a.harm, prep, dev, prec)
     ilu = None
     if a.op == "ilu":  # factor once; each call runs `--sweeps` ILU(0) iterations
         ilu = fnlh.DeviceIlu(dm, a.block, a.harm, precision=prec, device=dev)

@@ -239,3 +239,23 @@ def test_probe_library_exports_every_declared_symbol():
     assert lib.fnlh_probe_fma(0, 8, 1, 1, 100, 1, sink, ctypes.byref(ms), None) == -1  # threads
     assert lib.fnlh_probe_fma(0, 8, 1, 0, 256, 1, sink, ctypes.byref(ms), None) == -1  # blocks
     assert lib.fnlh_probe_fma(0, 8, 1, 1, 256, 1, None, ctypes.byref(ms), None) == -1  # sink
+
+
+def test_float_float_prep_and_solve_workspace_sizes():
+    """FNLH_PREP_FF adds the float-float copies of the blocks (8 bytes per
+    entry) to the prep blob; fnlh_solve_workspace_bytes adds the float-float
+    shadows of B and x ([n][C][b] FP32 pairs each) for the mixed precisions
+    only, and equals fnlh_workspace_bytes otherwise."""
+    n, nnz, b, N = 1000, 5400, 6, 4
+    C = 1 + 2 * N
+    base = fnlh.fnlh_prep_bytes(n, nnz, b, fnlh.FNLH_PREP_BF16)
+    ff = fnlh.fnlh_prep_bytes(n, nnz, b, fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF)
+    assert ff - base >= (nnz + n) * b * b * 8
+    for prec in (fnlh.FNLH_F32, fnlh.FNLH_BF16):
+        w = fnlh.fnlh_workspace_bytes(n, b, N, prec)
+        wf = fnlh.fnlh_solve_workspace_bytes(n, b, N, prec, fnlh.FNLH_PREP_FF | fnlh.FNLH_PREP_F32)
+        assert wf - w >= 2 * n * C * b * 8
+        assert fnlh.fnlh_solve_workspace_bytes(n, b, N, prec, fnlh.FNLH_PREP_F32) == w
+    w64 = fnlh.fnlh_workspace_bytes(n, b, N, fnlh.FNLH_F64)
+    assert fnlh.fnlh_solve_workspace_bytes(n, b, N, fnlh.FNLH_F64, fnlh.FNLH_PREP_FF) == w64
+    assert fnlh.fnlh_solve_workspace_bytes(n, 7, N, fnlh.FNLH_F32, fnlh.FNLH_PREP_FF) == 0

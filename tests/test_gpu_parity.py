@@ -468,3 +468,58 @@ def test_growing_iteration_is_reported_as_diverged(prec):
     st, checks, sweeps, rel = fnlh.fnlh_solve_batched(batch, prec, 1e-8, 10, 50, ws=ws, raise_on_error=False)
     assert st == fnlh.FNLH_ERR_DIVERGED, st
     assert checks <= 3
+
+
+FF_PREP = _gpu.ALL_PREP | fnlh.FNLH_PREP_FF
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_float_float_check_matches_fp64_check(prec):
+    """The float-float residual of a check agrees with the FP64 residual of
+    the same x: two checks with tol = 0 (never converged), so both runs make
+    the same first correction from the same FP64 first check, and the second
+    check -- float-float with FNLH_PREP_FF and the solve workspace, FP64
+    without -- measures the same x."""
+    p = inputs.problem((32, 24, 16), 6, 8, 20.0, name="c3_reduced")
+    dm, J, B = _gpu.device_problem(p, prep_flags=FF_PREP)
+    n = p.mesh.n_nodes
+    X1, X2 = torch.zeros_like(B), torch.zeros_like(B)
+    ws_ff = fnlh.solve_workspace(n, 6, p.n_harm, FF_PREP, "cuda", prec)
+    ws_64 = fnlh.workspace(n, 6, p.n_harm, "cuda", prec)
+    assert ws_ff.numel() > ws_64.numel()
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    st1, c1, s1, rel_ff = fnlh.fnlh_solve(dm, J, p.omega, B, X1, prec, 0.0, 12, 2, ws=ws_ff, flags=zg,
+                                          raise_on_error=False)
+    st2, c2, s2, rel_64 = fnlh.fnlh_solve(dm, J, p.omega, B, X2, prec, 0.0, 12, 2, ws=ws_64, flags=zg,
+                                          raise_on_error=False)
+    assert st1 == st2 == fnlh.FNLH_ERR_NOT_CONVERGED and c1 == c2 == 2 and s1 == s2 == 12
+    assert torch.equal(X1, X2)
+    assert np.all(rel_64 < 1e-2) and np.all(rel_64 > 1e-9)
+    assert np.allclose(rel_ff, rel_64, rtol=1e-6, atol=0), (rel_ff, rel_64)
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_float_float_checks_certified_solve(prec):
+    """A mixed solve with float-float checks converges in FP64 terms: the
+    oracle's residual of the returned x is at most 1e-8 per system, the
+    residual it reports (the confirming FP64 check) agrees with the oracle's,
+    and the solution is the FP64-checked solve's to 1e-6."""
+    p = inputs.problem((32, 24, 16), 6, 8, 20.0, name="c3_reduced")
+    dm, J, B = _gpu.device_problem(p, prep_flags=FF_PREP)
+    n = p.mesh.n_nodes
+    X = torch.empty_like(B)
+    Xr = torch.empty_like(B)
+    ws_ff = fnlh.solve_workspace(n, 6, p.n_harm, FF_PREP, "cuda", prec)
+    ws_64 = fnlh.workspace(n, 6, p.n_harm, "cuda", prec)
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40, ws=ws_ff, flags=zg)
+    st2, checks2, sweeps2, rel2 = fnlh.fnlh_solve(dm, J, p.omega, B, Xr, prec, 1e-8, 12, 40, ws=ws_64, flags=zg)
+    assert st == st2 == fnlh.FNLH_OK and np.all(rel <= 1e-8)
+    assert sweeps == sweeps2
+    oj = _gpu.oracle_jacobian(p)
+    x = X.cpu().numpy()
+    true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, x)
+    assert np.all(true_rel <= 1e-8), true_rel
+    assert np.allclose(rel, true_rel, rtol=1e-6, atol=1e-12)
+    err = _gpu.rel_err_per_system(x, Xr.cpu().numpy(), p.n_harm)
+    assert np.all(err <= 1e-6), err
