@@ -46,6 +46,68 @@ __device__ __forceinline__ void phase_shift(T (&re)[BS], T (&im)[BS], uint32_t s
   }
 }
 
+// ------------------------------------------------ internal vector layout
+//
+// Iterates and right-hand sides of the sweeps, in the rotated basis, per node
+// the systems' slices one after another: complex (re, im) pairs, the mean
+// flow (k = 0) with a zero imaginary part -- except for FP32 vectors of few
+// systems per node (K <= kRealMeanMaxSystems), where the mean flow keeps its
+// b real values alone (order: mean_pos), padded to kMeanSlot<BS> floats.
+// There the zero imaginary part would be a large share of the bytes (a
+// quarter at K = 2), and one thread carries all of a node's systems
+// (k_sweep_f32_node); with more systems the stored zeros cost less than the
+// selects the thread-per-(node, system) kernels would need.  The pad keeps
+// every slice on the alignment of its vector loads: 16 bytes for b = 6, 8
+// bytes for b = 5.
+constexpr int kRealMeanMaxSystems = 2;
+
+template <int BS>
+constexpr int kMeanSlot = ((2 * BS) % 4 == 0) ? (BS + 3) / 4 * 4 : (BS + 1) / 2 * 2;
+
+// Position of the mean flow's real value t in its FP32 slot: the first
+// kMeanSlot/2 values on the even positions, where a harmonic's slice keeps
+// its real parts, the rest on the odd positions from 1; the slot's other
+// positions hold zeros.
+template <int BS>
+__host__ __device__ constexpr int mean_pos(int t) {
+  return t < kMeanSlot<BS> / 2 ? 2 * t : 2 * (t - kMeanSlot<BS> / 2) + 1;
+}
+
+// Is slot position e of the FP32 mean flow a pad (zero)?
+template <int BS>
+__host__ __device__ constexpr bool mean_pad(int e) {
+  return (e & 1) ? (e >> 1) >= BS - kMeanSlot<BS> / 2 : false;
+}
+
+// Does a vector of type T with K systems per node keep the mean flow real?
+template <typename T>
+__host__ __device__ __forceinline__ bool real_mean(int K) {
+  return sizeof(T) == 4 && K <= kRealMeanMaxSystems;
+}
+
+template <int BS, typename T>
+__host__ __device__ __forceinline__ size_t node_stride(int K) {
+  return real_mean<T>(K) ? (size_t)kMeanSlot<BS> + (size_t)(K - 1) * 2 * BS : (size_t)K * 2 * BS;
+}
+
+template <int BS, typename T>
+__host__ __device__ __forceinline__ size_t sys_offset(int K, int k) {
+  if (!real_mean<T>(K)) return (size_t)k * 2 * BS;
+  return k == 0 ? 0 : (size_t)kMeanSlot<BS> + (size_t)(k - 1) * 2 * BS;
+}
+
+// element offset of system k's slice of node i
+template <int BS, typename T>
+__host__ __device__ __forceinline__ size_t slice_at(size_t i, int K, int k) {
+  return i * node_stride<BS, T>(K) + sys_offset<BS, T>(K, k);
+}
+
+// values stored for system k's slice: kMeanSlot for a real mean flow, else 2b
+template <int BS, typename T>
+__host__ __device__ __forceinline__ int slice_len(int K, int k) {
+  return (real_mean<T>(K) && k == 0) ? kMeanSlot<BS> : 2 * BS;
+}
+
 // ------------------------------------------------------------------ loads
 
 __device__ __forceinline__ float to_f(float x) { return x; }
@@ -322,7 +384,7 @@ __device__ __forceinline__ float2 ff_add_f(float2 a, float e) {
 // [0, 256)                      status words (int32)
 // [256, +partials)              residual partial sums  kResidualGrid x 2K doubles
 // norms                         final 2K doubles of the last residual
-// vec0, vec1, vec2              three [n][K][b] complex vectors (internal layout) in the precision's type
+// vec0, vec1, vec2              three vectors in the internal layout (node_stride) of the precision's type
 // pivinv                        FP64 only: [n][K][b] pairs (d, s) / (d^2 + s^2) of the shifted triangular solves
 struct WsLayout {
   size_t status, partials, norms, vec[3], pivinv, total, vec_bytes;

@@ -115,10 +115,10 @@ struct IluArgs {
   const double* vol;
   const float* offd32;  // Q_i^T J_ij Q_j in FP32 (FP32 smoother)
   const double* hess;   // Q_i^T (J_ii + D_i I) Q_i (FP32 smoother)
-  const float* r32;     // [n][K][b] complex Q^T r in FP32 (FP32 smoother)
+  const float* r32;     // Q^T r in FP32, internal FP32 layout (FP32 smoother)
   void* factor;         // [n][b*b][K] complex inverse pivots (T), systems innermost
   const double* r;      // [n][C][b] residual, caller layout
-  void* E;              // [n][K][b] complex work vector (T)
+  void* E;              // work vector (T), internal layout of T (common.cuh, node_stride)
   double* X;            // [n][C][b] iterate, caller layout
   int32_t* status;      // bit 1: a zero pivot
   int32_t masked;
@@ -276,12 +276,13 @@ __global__ void __launch_bounds__(kPivotThreads) k_ilu_pivots(const __grid_const
 template <int BS, typename T, bool kSubtract>
 __device__ __forceinline__ void ilu_gather(const IluArgs& a, int p, int cj, int k, T (&sr)[BS], T (&si)[BS]) {
   const int j = col_of(cj);
-  const T* yj = (const T*)a.E + ((size_t)j * a.K + k) * 2 * BS;
+  const T* yj = (const T*)a.E + slice_at<BS, T>(j, a.K, k);
+  const bool real = real_mean<T>(a.K) && k == 0;  // a real mean flow
   T xr[BS], xi[BS];
 #pragma unroll
   for (int t = 0; t < BS; ++t) {
-    xr[t] = yj[2 * t];
-    xi[t] = yj[2 * t + 1];
+    xr[t] = real ? yj[mean_pos<BS>(t)] : yj[2 * t];
+    xi[t] = real ? T(0) : yj[2 * t + 1];
   }
   if (side_of(cj)) phase_shift<BS, T>(xr, xi, side_of(cj), a.sys.phase[k]);
   // FP64, b = 6 with frozen turbulence: rows 0..4 of the original-basis
@@ -345,6 +346,25 @@ __device__ __forceinline__ void ilu_pivot_apply(const T* __restrict__ F, int K, 
   }
 }
 
+// One system's slice of the work vector in the internal layout (common.cuh,
+// node_stride): complex pairs, or for a real mean flow its values (the pivot
+// of the real system gives a zero imaginary part) and the pad.
+template <int BS, typename T>
+__device__ __forceinline__ void store_e(T* __restrict__ e, bool real, const T (&yr)[BS], const T (&yi)[BS]) {
+  if (real) {
+#pragma unroll
+    for (int q = 0; q < BS; ++q) e[mean_pos<BS>(q)] = yr[q];
+    for (int t = 0; t < kMeanSlot<BS>; ++t)
+      if (mean_pad<BS>(t)) e[t] = T(0);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+    e[2 * q] = yr[q];
+    e[2 * q + 1] = yi[q];
+  }
+}
+
 // Forward pass over one colour: z_i = P_i^-1 (r_i - sum_{j earlier} A_ij z_j).
 // The top colour has no later neighbours, so its backward pass would only
 // copy y_i = z_i: in FP64 this pass adds it to x_i instead, and the
@@ -357,18 +377,20 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_consta
   if (t >= a.end) return;
   const int i = a.order[t];
   if (!ilu_active(a, k)) {  // a frozen system: no correction
-    T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
+    T* e = (T*)a.E + slice_at<BS, T>(i, a.K, k);
+    const int len = slice_len<BS, T>(a.K, k);
 #pragma unroll
-    for (int q = 0; q < 2 * BS; ++q) e[q] = T(0);
+    for (int q = 0; q < 2 * BS; ++q)
+      if (q < len) e[q] = T(0);
     return;
   }
   T sr[BS], si[BS];
   if constexpr (sizeof(T) == 4) {
-    const float* rp = a.r32 + ((size_t)i * a.K + k) * 2 * BS;
+    const float* rp = a.r32 + slice_at<BS, float>(i, a.K, k);
 #pragma unroll
     for (int q = 0; q < BS; ++q) {
-      sr[q] = rp[2 * q];
-      si[q] = rp[2 * q + 1];
+      sr[q] = real_mean<float>(a.K) && k == 0 ? rp[mean_pos<BS>(q)] : rp[2 * q];
+      si[q] = real_mean<float>(a.K) && k == 0 ? 0.0f : rp[2 * q + 1];
     }
   } else {
     const int c0 = (k == 0) ? 0 : 2 * k - 1;
@@ -387,12 +409,7 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_forward(const __grid_consta
   }
   T yr[BS], yi[BS];
   ilu_pivot_apply<BS, T>((const T*)a.factor + pivot_at(i, 0, k, a.K, BS), a.K, sr, si, yr, yi);
-  T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
-#pragma unroll
-  for (int q = 0; q < BS; ++q) {
-    e[2 * q] = yr[q];
-    e[2 * q + 1] = yi[q];
-  }
+  store_e<BS, T>((T*)a.E + slice_at<BS, T>(i, a.K, k), real_mean<T>(a.K) && k == 0, yr, yi);
   if constexpr (sizeof(T) == 8) {  // FP32: x += Q e after the passes
     if (a.last) {
       double* xp = a.X + ((size_t)i * a.sys.C + ((k == 0) ? 0 : 2 * k - 1)) * BS;
@@ -428,12 +445,13 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_const
     ilu_gather<BS, T, false>(a, p, cj, k, sr, si);
     any = true;
   }
-  T* e = (T*)a.E + ((size_t)i * a.K + k) * 2 * BS;
+  T* e = (T*)a.E + slice_at<BS, T>(i, a.K, k);
+  const bool real = real_mean<T>(a.K) && k == 0;  // a real mean flow
   T yr[BS], yi[BS];
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
-    yr[q] = e[2 * q];
-    yi[q] = e[2 * q + 1];
+    yr[q] = real ? e[mean_pos<BS>(q)] : e[2 * q];
+    yi[q] = real ? T(0) : e[2 * q + 1];
   }
   if (any) {
     T dr[BS], di[BS];
@@ -442,9 +460,8 @@ __global__ void __launch_bounds__(kIluThreads) k_ilu_backward(const __grid_const
     for (int q = 0; q < BS; ++q) {
       yr[q] -= dr[q];
       yi[q] -= di[q];
-      e[2 * q] = yr[q];
-      e[2 * q + 1] = yi[q];
     }
+    store_e<BS, T>(e, real, yr, yi);
   }
   if constexpr (sizeof(T) == 8) {  // FP32: x += Q e after the passes
     double* xp = a.X + ((size_t)i * a.sys.C + ((k == 0) ? 0 : 2 * k - 1)) * BS;

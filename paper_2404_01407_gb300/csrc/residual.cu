@@ -28,7 +28,7 @@ struct ResArgs {
   const double* B;
   const double* X;
   double* r;        // nullable [n][C][b]
-  float* r32rot;    // nullable [n][K][b] complex: Q_i^T r_i in FP32 (r rounded to FP32 first)
+  float* r32rot;    // nullable, internal FP32 layout: Q_i^T r_i in FP32 (r rounded to FP32 first)
   const float* rotf;  // Q_i in FP32 (with r32rot)
   const int32_t* info;  // prep info word, nullable: 0 = the b = 6 frozen-turbulence pattern holds
   int32_t x_zero;     // x is zero: r = B without reading X
@@ -166,9 +166,8 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
     }
   }
   if (a.r32rot) {
-    // Q_i^T r in the sweeps' internal layout [n][K][b] complex, in FP32:
-    // the inner solve only needs r to FP32 accuracy (the mean flow's
-    // imaginary part is written as an exact zero)
+    // Q_i^T r in the sweeps' internal FP32 layout (common.cuh, node_stride):
+    // the inner solve only needs r to FP32 accuracy
     const float* Q = a.rotf + (size_t)i * BS * BS;
     float fr[BS], fi[BS];
 #pragma unroll
@@ -176,7 +175,8 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
       fr[t] = (float)rr[t];
       fi[t] = (float)ri[t];
     }
-    float* rp = a.r32rot + ((size_t)i * a.sys.K + k) * 2 * BS;
+    float* rp = a.r32rot + slice_at<BS, float>(i, a.sys.K, k);
+    const bool real = real_mean<float>(a.sys.K) && k == 0;
 #pragma unroll
     for (int q = 0; q < BS; ++q) {
       float ar = 0.0f, ai = 0.0f;
@@ -186,9 +186,16 @@ __device__ __forceinline__ void residual_pair(const ResArgs& a, int i, int k, do
         ar += qv * fr[t];
         ai += qv * fi[t];
       }
-      rp[2 * q] = ar;
-      rp[2 * q + 1] = cplx ? ai : 0.0f;
+      if (real) {
+        rp[mean_pos<BS>(q)] = ar;
+      } else {
+        rp[2 * q] = ar;
+        rp[2 * q + 1] = cplx ? ai : 0.0f;
+      }
     }
+    if (real)
+      for (int e = 0; e < kMeanSlot<BS>; ++e)
+        if (mean_pad<BS>(e)) rp[e] = 0.0f;
   }
 }
 
@@ -352,9 +359,16 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual_ff(const __grid_c
           o_im += qc[t].x * vi;
         }
         if (valid) {
-          float* rp = a.r32rot + ((size_t)i * K + k) * 2 * BS;
-          rp[2 * q] = o_re;
-          rp[2 * q + 1] = (k > 0) ? o_im : 0.0f;
+          float* rp = a.r32rot + slice_at<BS, float>(i, K, k);
+          if (!real_mean<float>(K) || k > 0) {
+            rp[2 * q] = o_re;
+            rp[2 * q + 1] = (k > 0) ? o_im : 0.0f;
+          } else {  // a real mean flow: its values, then the pad
+            rp[mean_pos<BS>(q)] = o_re;
+            if (q == BS - 1)
+              for (int e = 0; e < kMeanSlot<BS>; ++e)
+                if (mean_pad<BS>(e)) rp[e] = 0.0f;
+          }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {

@@ -14,7 +14,8 @@
 // The sweeps run in the per-node Hessenberg basis prepared by
 // fnlh_prepare (x = Q x~), where the diagonal block of system k is
 // H_i + i omega_k V_i I and its solve costs O(b^2).  Iterates live in the
-// internal complex-interleaved layout [n][K][b]; the rotate kernels move
+// internal layout (common.cuh, node_stride: complex pairs per system, the
+// mean flow real in FP32 vectors of K <= 2 systems); the rotate kernels move
 // between it and the caller's [n][C][b] layout.
 #include <cuda_runtime.h>
 
@@ -68,7 +69,194 @@ __global__ void __launch_bounds__(kSweepThreadsF32, 16) k_sweep_f32(const __grid
   sweep_tile_f32<BS, TJ>(a.row, io, (long long)blockIdx.x * blockDim.x, a.x_zero != 0, smem, a.smem_floats);
 }
 
-// Caller layout [n][C][b] (FP64) -> internal [n][K][b] complex, y = Q_i^T x,
+// ------------------------------------------- FP32, few systems per node
+
+constexpr int kNodeThreads = 128;
+constexpr int kNodeMaxSystems = kRealMeanMaxSystems;  // K up to this: one thread per node
+
+// `COUNT` floats from a 16- (COUNT % 4 == 0) or 8-byte aligned (COUNT even) address.
+template <int COUNT>
+__device__ __forceinline__ void load_floats(const float* __restrict__ p, float (&v)[COUNT]) {
+  if constexpr (COUNT % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < COUNT / 4; ++q) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+      v[4 * q] = f.x;
+      v[4 * q + 1] = f.y;
+      v[4 * q + 2] = f.z;
+      v[4 * q + 3] = f.w;
+    }
+  } else {
+    static_assert(COUNT % 2 == 0, "node slices are padded to an even length");
+#pragma unroll
+    for (int q = 0; q < COUNT / 2; ++q) {
+      const float2 f = __ldg(reinterpret_cast<const float2*>(p) + q);
+      v[2 * q] = f.x;
+      v[2 * q + 1] = f.y;
+    }
+  }
+}
+
+template <int COUNT>
+__device__ __forceinline__ void store_floats(float* __restrict__ p, const float (&v)[COUNT]) {
+  if constexpr (COUNT % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < COUNT / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < COUNT / 2; ++q) reinterpret_cast<float2*>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
+// One whole BS x BS block as raw words, issued as one batch of the widest
+// loads its alignment allows (block p starts at p * BS^2 * sizeof(TJ) bytes).
+template <int BS, typename TJ>
+struct RawBlock {
+  static constexpr int kBytes = BS * BS * (int)sizeof(TJ);
+  static constexpr int kWords = (kBytes + 3) / 4;
+  uint32_t w[kWords];
+  __device__ __forceinline__ void load(const TJ* __restrict__ blk) {
+    if constexpr (kBytes % 16 == 0) {
+#pragma unroll
+      for (int q = 0; q < kBytes / 16; ++q) {
+        const uint4 f = __ldg(reinterpret_cast<const uint4*>(blk) + q);
+        w[4 * q] = f.x;
+        w[4 * q + 1] = f.y;
+        w[4 * q + 2] = f.z;
+        w[4 * q + 3] = f.w;
+      }
+    } else if constexpr (kBytes % 8 == 0) {
+#pragma unroll
+      for (int q = 0; q < kBytes / 8; ++q) {
+        const uint2 f = __ldg(reinterpret_cast<const uint2*>(blk) + q);
+        w[2 * q] = f.x;
+        w[2 * q + 1] = f.y;
+      }
+    } else if constexpr (kBytes % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < kWords; ++q) w[q] = __ldg(reinterpret_cast<const uint32_t*>(blk) + q);
+    } else {  // BF16 with odd BS: 2-byte alignment only
+      const uint16_t* h = reinterpret_cast<const uint16_t*>(blk);
+#pragma unroll
+      for (int q = 0; q < kWords; ++q) {
+        const uint32_t lo = __ldg(h + 2 * q);
+        const uint32_t hi = (2 * q + 1 < BS * BS) ? (uint32_t)__ldg(h + 2 * q + 1) : 0u;
+        w[q] = lo | (hi << 16);
+      }
+    }
+  }
+  // entry e of the row-major block, as FP32
+  __device__ __forceinline__ float at(int e) const {
+    if constexpr (sizeof(TJ) == 2) return (e & 1) ? bf16_hi(w[e >> 1]) : bf16_lo(w[e >> 1]);
+    else return __uint_as_float(w[e]);
+  }
+};
+
+// A node's FP32 slices (the mean flow's padded reals, then (re, im) pairs)
+// into one complex vector per system, the mean flow's imaginary part zero.
+template <int BS, int KS, int V>
+__device__ __forceinline__ void unpack_node(const float (&v)[V], Cvec<BS, float> (&c)[KS]) {
+#pragma unroll
+  for (int t = 0; t < BS; ++t) {
+    c[0].re[t] = v[mean_pos<BS>(t)];
+    c[0].im[t] = 0.0f;
+  }
+#pragma unroll
+  for (int k = 1; k < KS; ++k)
+#pragma unroll
+    for (int t = 0; t < BS; ++t) {
+      c[k].re[t] = v[kMeanSlot<BS> + (k - 1) * 2 * BS + 2 * t];
+      c[k].im[t] = v[kMeanSlot<BS> + (k - 1) * 2 * BS + 2 * t + 1];
+    }
+}
+
+// FP32 arithmetic for few systems per node (K <= kNodeMaxSystems, vectors
+// with a real mean flow: common.cuh, real_mean): one
+// thread per node carries every system, so each off-diagonal block is loaded
+// once, whole, and applied from registers to the mean flow's real column and
+// to every harmonic's (re, im) pair -- instead of each of the node's K
+// threads loading it row by row.  Per system the operations and their order
+// are those of the thread-per-(node, system) tile (sweep_tile_f32), so the
+// two kernels give the same values.
+template <int BS, typename TJ, int KS>
+__global__ void __launch_bounds__(kNodeThreads) k_sweep_f32_node(const __grid_constant__ SweepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TileRow& R = a.row;
+  if (i >= R.n) return;
+  constexpr int M = kMeanSlot<BS>;
+  constexpr int V = M + (KS - 1) * 2 * BS;  // floats of one node's slices
+  const SweepIO io{a.Xin, a.Xout, a.omega, a.masked ? a.active : nullptr, a.phase};
+  const bool x_zero = a.x_zero != 0;
+  Cvec<BS, float> s[KS];
+  {
+    float v[V];
+    load_floats<V>((const float*)R.Bt + (size_t)i * V, v);
+    unpack_node<BS, KS>(v, s);
+  }
+  if (!x_zero) {
+    const float* __restrict__ X = (const float*)io.Xin;
+    const int p0 = __ldg(R.row_ptr + i), p1 = __ldg(R.row_ptr + i + 1);
+    for (int p = p0; p < p1; ++p) {
+      const int cj = __ldg(R.col_idx + p);
+      if (cut_of(cj)) continue;  // coupling to another partition: dropped
+      float v[V];
+      load_floats<V>(X + (size_t)col_of(cj) * V, v);
+      RawBlock<BS, TJ> J;
+      J.load((const TJ*)R.offd + (size_t)p * BS * BS);
+      Cvec<BS, float> x[KS];
+      unpack_node<BS, KS>(v, x);
+      if (side_of(cj)) {
+#pragma unroll
+        for (int k = 0; k < KS; ++k) phase_shift<BS, float>(x[k].re, x[k].im, side_of(cj), io.phase[k]);
+      }
+#pragma unroll
+      for (int r = 0; r < BS; ++r)
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+          const float jv = J.at(r * BS + t);
+#pragma unroll
+          for (int k = 0; k < KS; ++k) {
+            s[k].re[r] -= jv * x[k].re[t];
+            if (k > 0) s[k].im[r] -= jv * x[k].im[t];  // the mean flow's stays zero
+          }
+        }
+    }
+  }
+  const float* H = (const float*)R.hess + (size_t)i * BS * BS;
+  const double vol = __ldg(R.vol + i);
+  const float* xin = (const float*)io.Xin + (size_t)i * V;
+  float out[V];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int o = (k == 0) ? 0 : M + (k - 1) * 2 * BS;
+    if (sys_active(io, k)) {
+      hess_solve<BS, float>(H, (float)(io.omega[k] * vol), s[k].re, s[k].im);
+#pragma unroll
+      for (int t = 0; t < BS; ++t) {
+        if (k == 0) {
+          out[mean_pos<BS>(t)] = s[0].re[t];
+        } else {
+          out[o + 2 * t] = s[k].re[t];
+          out[o + 2 * t + 1] = s[k].im[t];
+        }
+      }
+      if (k == 0) {
+#pragma unroll
+        for (int e = 0; e < M; ++e)
+          if (mean_pad<BS>(e)) out[e] = 0.0f;
+      }
+    } else {  // a frozen (converged) system keeps its iterate
+      const int len = (k == 0) ? M : 2 * BS;
+#pragma unroll
+      for (int t = 0; t < 2 * BS; ++t)
+        if (t < len) out[o + t] = x_zero ? 0.0f : xin[o + t];
+    }
+  }
+  store_floats<V>((float*)io.Xout + (size_t)i * V, out);
+}
+
+// Caller layout [n][C][b] (FP64) -> internal layout, y = Q_i^T x,
 // one thread per (node, system).
 template <int BS, typename TO>
 __global__ void __launch_bounds__(256) k_rotate_in(long long count, int K, const double* __restrict__ rot,
@@ -86,7 +274,8 @@ __global__ void __launch_bounds__(256) k_rotate_in(long long count, int K, const
     vr[t] = xr[t];
     vi[t] = (k == 0) ? 0.0 : xr[BS + t];
   }
-  TO* out = y + g * 2 * BS;
+  TO* out = y + slice_at<BS, TO>(i, K, k);
+  const bool real = real_mean<TO>(K) && k == 0;  // a real mean flow: its values, then the pad
 #pragma unroll
   for (int r = 0; r < BS; ++r) {
     double ar = 0.0, ai = 0.0;
@@ -96,12 +285,19 @@ __global__ void __launch_bounds__(256) k_rotate_in(long long count, int K, const
       ar += q * vr[t];
       ai += q * vi[t];
     }
-    out[2 * r] = (TO)ar;
-    out[2 * r + 1] = (TO)ai;
+    if (real) {
+      out[mean_pos<BS>(r)] = (TO)ar;
+    } else {
+      out[2 * r] = (TO)ar;
+      out[2 * r + 1] = (TO)ai;
+    }
   }
+  if (real)
+    for (int e = 0; e < kMeanSlot<BS>; ++e)
+      if (mean_pad<BS>(e)) out[e] = TO(0);
 }
 
-// Internal [n][K][b] complex -> caller layout (FP64), x (+)= Q_i y.
+// Internal layout -> caller layout (FP64), x (+)= Q_i y.
 template <int BS, typename TI>
 __global__ void __launch_bounds__(256) k_rotate_out(long long count, int K, const double* __restrict__ rot,
                                                     const TI* __restrict__ y, double* __restrict__ x, int accumulate) {
@@ -111,12 +307,13 @@ __global__ void __launch_bounds__(256) k_rotate_out(long long count, int K, cons
   const int k = (int)(g - i * K);
   const int C = 2 * K - 1;
   const double* Q = rot + i * BS * BS;
-  const TI* in = y + g * 2 * BS;
+  const TI* in = y + slice_at<BS, TI>(i, K, k);
+  const bool real = real_mean<TI>(K) && k == 0;  // a real mean flow
   double vr[BS], vi[BS];
 #pragma unroll
   for (int t = 0; t < BS; ++t) {
-    vr[t] = (double)in[2 * t];
-    vi[t] = (double)in[2 * t + 1];
+    vr[t] = (double)(real ? in[mean_pos<BS>(t)] : in[2 * t]);
+    vi[t] = real ? 0.0 : (double)in[2 * t + 1];
   }
   double* xr = x + (i * C + (k == 0 ? 0 : 2 * k - 1)) * BS;
 #pragma unroll
@@ -148,12 +345,13 @@ __global__ void __launch_bounds__(256) k_update_f32(long long count, int K, cons
   const int k = (int)(g - i * K);
   const int C = 2 * K - 1;
   const float* Q = rotf + i * BS * BS;
-  const float* in = y + g * 2 * BS;
+  const float* in = y + slice_at<BS, float>(i, K, k);
+  const bool real = real_mean<float>(K) && k == 0;  // a real mean flow
   float vr[BS], vi[BS];
 #pragma unroll
   for (int t = 0; t < BS; ++t) {
-    vr[t] = in[2 * t];
-    vi[t] = in[2 * t + 1];
+    vr[t] = real ? in[mean_pos<BS>(t)] : in[2 * t];
+    vi[t] = real ? 0.0f : in[2 * t + 1];
   }
   // All loads of the read-modify-write are issued before any store, so one
   // memory round trip covers the whole update of this (node, system).
@@ -360,6 +558,10 @@ int sweep_launch(const SweepArgs& a, size_t smem_bytes, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
     const int warps = std::min(a.row.K, kSweepThreads / 32);
     k_sweep_f64<BS><<<(unsigned)((a.row.n + 31) / 32), 32 * warps, 0, s>>>(a);
+  } else if (a.row.K <= kNodeMaxSystems) {
+    const unsigned grid = blocks_for(a.row.n, kNodeThreads);
+    if (a.row.K == 1) k_sweep_f32_node<BS, TJ, 1><<<grid, kNodeThreads, 0, s>>>(a);
+    else k_sweep_f32_node<BS, TJ, 2><<<grid, kNodeThreads, 0, s>>>(a);
   } else {
     k_sweep_f32<BS, TJ><<<blocks_for(count, kSweepThreadsF32), kSweepThreadsF32, smem_bytes, s>>>(a);
   }
@@ -716,6 +918,12 @@ struct BatchPlan {
   SweepOperands ops[kMaxBatchRows];
   Systems sys[kMaxBatchRows];
   char* base[kMaxBatchRows];  // the row's workspace slice (ws_layout of its size and precision)
+  const fnlh_mesh* mesh[kMaxBatchRows];
+  // FP32 rows of K <= kRealMeanMaxSystems (vectors with a real mean flow):
+  // swept by their own single-row launches (k_sweep_f32_node), not in the
+  // shared tiles
+  bool own[kMaxBatchRows];
+  int n_rows;
 };
 
 template <int BS, typename TJ, typename T>
@@ -731,13 +939,15 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
   size_t off = 256;
   long long tiles = 0;
   int kmin = kMaxSys;
-  a.n_rows = n_rows;
+  P.n_rows = n_rows;
   for (int r = 0; r < n_rows; ++r) {
     const fnlh_row& R = rows[r];
     int rc = sweep_operands(R.mesh, R.J, precision, &P.ops[r]);
     if (rc) return rc;
     P.sys[r] = make_systems(R.n_harm, R.omega, R.sigma);
     const Systems& sys = P.sys[r];
+    P.mesh[r] = R.mesh;
+    P.own[r] = real_mean<T>(sys.K);
     const WsLayout W = ws_layout(R.mesh->n_nodes, BS, R.n_harm, precision);
     char* base = (char*)ws + off;
     P.base[r] = base;
@@ -768,20 +978,22 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
   // (FP32 with K >= kStageMinSystems), then the rest.  Each group gets its
   // own launch per sweep, so that the rows that read their blocks through L1
   // do not run on SMs configured for the staged rows' shared memory (mixing
-  // them in one launch cost 3% on three rows with K = 3, 9, 5).
+  // them in one launch cost 3% on three rows with K = 3, 9, 5).  Rows swept
+  // by their own launches (P.own) take no tiles.
   int q = 0;
   P.split = 0;
   for (int pass = 0; pass < 2; ++pass)
     for (int r = 0; r < n_rows; ++r) {
       BatchRow& D = a.row[r];
       const bool staged = sizeof(T) == 4 && D.row.stage;
-      if (staged != (pass == 0)) continue;
+      if (P.own[r] || staged != (pass == 0)) continue;
       a.order[q++] = r;
       D.tile0 = tiles;
       tiles += ((long long)D.row.n * D.row.K + P.threads - 1) / P.threads;
       if (pass == 0) P.split = tiles;
     }
   P.n_tiles = tiles;
+  a.n_rows = q;  // rows in the tile list
   P.smem = 0;
   P.persistent = ctas_per_sm > 0;
   if constexpr (sizeof(T) == 4) {
@@ -803,11 +1015,26 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
 }
 
 // `sweeps` launches starting at a.parity (the first from zero when x_zero);
-// a.parity holds the buffer of the result on return.
+// a.parity holds the buffer of the result on return.  The rows that sweep on
+// their own (P.own) run all their sweeps first, between the same buffers.
 template <int BS, typename TJ, typename T>
 int batch_launch(BatchArgs& a, const BatchPlan& P, int sweeps, int x_zero, cudaStream_t s) {
   int rc = mark(g_ev_begin, s);
   if (rc) return rc;
+  {
+    cudaEvent_t b = g_ev_begin, e = g_ev_end;  // the hook brackets the whole batch
+    g_ev_begin = g_ev_end = nullptr;
+    for (int r = 0; r < P.n_rows && !rc; ++r) {
+      if (!P.own[r]) continue;
+      const BatchRow& D = a.row[r];
+      T* res = nullptr;
+      rc = run_sweeps<BS, TJ, T>(P.mesh[r], P.ops[r], P.sys[r], (const T*)D.row.Bt, (T*)D.x[a.parity],
+                                 (T*)D.x[a.parity ^ 1], sweeps, x_zero, s, &res, D.masked ? D.active : nullptr);
+    }
+    g_ev_begin = b;
+    g_ev_end = e;
+    if (rc) return rc;
+  }
   for (int it = 0; it < sweeps; ++it) {
     a.x_zero = (it == 0) ? x_zero : 0;
     for (int g = 0; g < 2; ++g) {  // the staged rows' tiles, then the others'

@@ -4,7 +4,9 @@
 // One thread per (node, system).  The iterate and right-hand side use the
 // library's internal layout [n][K][b] of complex (re, im) pairs in the
 // per-node Hessenberg basis (the mean flow, system 0, carries a zero
-// imaginary part), so each thread's slice is one contiguous vector.
+// imaginary part), so each thread's slice is one contiguous vector.  (FP32
+// vectors of K <= kRealMeanMaxSystems systems keep the mean flow real
+// instead, common.cuh; they are swept only by k_sweep_f32_node.)
 //
 // A CTA owns a tile of consecutive (node, system) pairs.  In the staged form
 // (low-precision blocks, FP32 arithmetic) the CTA first copies the
@@ -478,7 +480,8 @@ __device__ __forceinline__ void spmv_rows_global(const TJ* __restrict__ jb, cons
   }
 }
 
-// Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0.
+// Staged FP32 form: one tile of blockDim.x consecutive pairs starting at g0,
+// for rows of more than kRealMeanMaxSystems systems (complex slices only).
 // Every thread of the CTA must call this (it synchronises).
 template <int BS, typename TJ>
 __device__ __forceinline__ void sweep_tile_f32(const TileRow& R, const SweepIO& io, long long g0, bool x_zero,
