@@ -62,7 +62,7 @@ def _compile(src: str, extra) -> str:
 
 def _link(objs, out):
     tmp = out + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"]  # -ldl: NVTX loads its tool
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

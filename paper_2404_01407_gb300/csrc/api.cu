@@ -7,6 +7,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace fnlh {
@@ -103,6 +105,16 @@ int check_pairs(int n_nodes, int n_harm) {
 
 }  // namespace
 
+// Named NVTX range over one entry point, so that a profiler's timeline (or
+// ncu --nvtx-include) shows each library call as one span.  NVTX is
+// header-only: without an attached tool a push/pop is a few instructions.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 #define FNLH_TRY(expr)       \
   do {                       \
     int _rc = (expr);        \
@@ -187,6 +199,7 @@ size_t fnlh_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm, int3
 
 int fnlh_build_jacobian(const fnlh_mesh* mesh, const double* Q, const fnlh_params* params, fnlh_jacobian* J,
                         fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_build_jacobian");
   FNLH_TRY(check_mesh(mesh, true));
   FNLH_TRY(check_jac(mesh, J));
   if (!params || (mesh->n_nodes > 0 && !Q)) return FNLH_ERR_ARG;
@@ -201,6 +214,7 @@ int fnlh_build_jacobian(const fnlh_mesh* mesh, const double* Q, const fnlh_param
 }
 
 int fnlh_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_prepare");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!J->prep) return FNLH_ERR_WORKSPACE;
@@ -218,6 +232,7 @@ int fnlh_prepare(const fnlh_mesh* mesh, fnlh_jacobian* J, fnlh_stream_t stream) 
 int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
                const double* sigma, const double* B, double* X, int32_t sweeps, int32_t precision, void* workspace,
                size_t workspace_bytes, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_relax");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || sweeps < 0) return FNLH_ERR_ARG;
@@ -233,6 +248,7 @@ int fnlh_relax(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
 int fnlh_residual(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
                   const double* sigma, const double* B, const double* X, double* r, double* norms, void* workspace,
                   size_t workspace_bytes, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_residual");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, sigma));
@@ -250,6 +266,7 @@ int fnlh_solve(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, co
                const double* sigma, const double* B, double* X, int32_t precision, double tol, int32_t inner_sweeps,
                int32_t max_checks, int32_t flags, void* workspace, size_t workspace_bytes, int32_t* checks_done,
                int32_t* sweeps_done, double* rel_res, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_solve");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   if (!valid_precision(precision) || !(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
@@ -268,6 +285,7 @@ size_t fnlh_batched_extra_bytes(int32_t n_rows) { return n_rows > 0 ? batched_ex
 
 int fnlh_relax_batched(const fnlh_row* rows, int32_t n_rows, int32_t sweeps, int32_t precision,
                        const fnlh_tuning* tuning, void* workspace, size_t workspace_bytes, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_relax_batched");
   if (!rows || n_rows < 1 || sweeps < 0 || !valid_precision(precision)) return FNLH_ERR_ARG;
   size_t need = batched_extra_bytes(n_rows);
   for (int r = 0; r < n_rows; ++r) {
@@ -291,6 +309,7 @@ int fnlh_solve_batched(const fnlh_row* rows, int32_t n_rows, int32_t precision, 
                        int32_t max_checks, int32_t flags, const fnlh_tuning* tuning, void* workspace,
                        size_t workspace_bytes, int32_t* checks_done, int32_t* sweeps_done, double* rel_res,
                        fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_solve_batched");
   if (!rows || n_rows < 1 || !valid_precision(precision)) return FNLH_ERR_ARG;
   if (!(tol >= 0.0) || inner_sweeps < 1 || max_checks < 1) return FNLH_ERR_ARG;
   if (flags & ~(FNLH_SOLVE_ZERO_GUESS | FNLH_SOLVE_MASK_CONVERGED)) return FNLH_ERR_ARG;
@@ -318,6 +337,7 @@ int fnlh_solve_batched(const fnlh_row* rows, int32_t n_rows, int32_t precision, 
 int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,
                           const double* sigma, const double* B, const double* X, double* r, double* norms,
                           fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_residual_noalloc");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, sigma));
@@ -377,6 +397,7 @@ static int check_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_i
 
 int fnlh_ilu_factor(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega, fnlh_ilu* ilu,
                     void* workspace, size_t workspace_bytes, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_ilu_factor");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, nullptr));
@@ -398,6 +419,7 @@ int fnlh_solve_ilu(const fnlh_mesh* mesh, const fnlh_jacobian* J, const fnlh_ilu
                    const double* omega, const double* sigma, const double* B, double* X, double tol,
                    int32_t max_iterations, int32_t flags, void* workspace, size_t workspace_bytes,
                    int32_t* iterations_done, double* rel_res, fnlh_stream_t stream) {
+  NvtxRange range_("fnlh_solve_ilu");
   FNLH_TRY(check_mesh(mesh, false));
   FNLH_TRY(check_jac(mesh, J));
   FNLH_TRY(check_systems(n_harm, omega, sigma));
