@@ -250,14 +250,16 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_cons
 // of ||B|| keeps ~5 significant digits.  Mapping: a warp takes kFfNodes
 // nodes and a lane one row q of one node (30 lanes busy), so that a block's
 // rows are read by consecutive lanes and each row, held in registers, serves
-// up to kFfSys systems; the rotation Q_i^T r to the sweeps' basis gathers the
+// up to kFfSys systems (two: with four 256-thread CTAs per SM at 64 registers
+// the c3 mixed solves ran 1.2-1.7% faster than with four systems at 80
+// registers and three CTAs); the rotation Q_i^T r to the sweeps' basis gathers the
 // node's rows with shuffles.  Writes Q_i^T r (FP32) like the FP64 kernel, and
 // per block the sums ||r_k||^2 and ||B_k||^2 (from B's high parts) in a
 // fixed order.  Not for meshes with periodic edges (no phase factors here).
-constexpr int kFfSys = 4;
+constexpr int kFfSys = 2;
 
 template <int BS>
-__global__ void __launch_bounds__(kResidualThreads) k_residual_ff(const __grid_constant__ ResArgs a) {
+__global__ void __launch_bounds__(kResidualThreads, 4) k_residual_ff(const __grid_constant__ ResArgs a) {
   constexpr int kNodes = 30 / BS;  // nodes per warp: 5 for b = 6, 6 for b = 5
   constexpr int kWarps = kResidualThreads / 32;
   __shared__ double s_acc[kWarps][2 * kMaxSys];
