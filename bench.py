@@ -46,6 +46,7 @@ METRIC = "node·harmonic updates/s per Jacobi sweep; mixed vs FP64 time-to-1e-8 
 UNIT = "updates/s"
 SWEEPS = 50
 WORKLOAD = "c2"
+BF16_INNER = 21  # BF16-block inner sweeps per correction (FP32 blocks: 30)
 
 # FP64 peak from unit counts and clocks (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz): context only; the
 # roofline is taken against the FP64 peak the multiply-add probe measures on the same GPU in the same run
@@ -556,7 +557,9 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
            "unit": "s", "higher_is_better": False}
     # inner sweeps per FP64 residual: the best of a scan of 10..40 on this workload (every run needs
     # ~60 sweeps; each extra check costs one FP64 residual)
-    cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)]
+    # inner sweeps per correction: the fewest that keep the fewest corrections (scanned on GB300: FP32 29
+    # and BF16 20 each need one more check on every workload here)
+    cases = [("f64", fnlh.FNLH_F64, 10), ("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, BF16_INNER)]
     zg = fnlh.FNLH_SOLVE_ZERO_GUESS
     sols = {}
     for name, prec, inner in cases:
@@ -570,19 +573,23 @@ def time_to_1e8_section(torch, fnlh, inputs, dev, with_oracle=True, tol=1e-8):
         t = time.perf_counter() - t0
         # end to end through the public API: B up from pinned host memory, the solve, x down
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
         B.copy_(Bh, non_blocking=True)
+        ev[1].record()
         fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, tol, inner, 200, ws=w, raise_on_error=False, flags=zg)
+        ev[2].record()
         Xh.copy_(X, non_blocking=True)
-        e1.record()
+        ev[3].record()
         torch.cuda.synchronize()
+        e0, e1 = ev[0], ev[3]
         sols[name] = Xh.numpy().copy()
         out[name] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks, "sweeps": sweeps,
                      "inner_sweeps": inner, "max_rel_residual": float(np.max(rel)),
                      "rel_residual_per_system": [float(v) for v in rel],
                      "e2e": {"seconds": e0.elapsed_time(e1) * 1e-3, "h2d_bytes": Bh.numel() * 8,
-                             "d2h_bytes": Xh.numel() * 8}}
+                             "d2h_bytes": Xh.numel() * 8, "h2d_ms": ev[0].elapsed_time(ev[1]),
+                             "solve_ms": ev[1].elapsed_time(ev[2]), "d2h_ms": ev[2].elapsed_time(ev[3])}}
     # the same mixed solves with every check in FP64 (the plain-size workspace has no float-float shadows)
     for name, prec, inner in cases[1:]:
         w = fnlh.workspace(n, b, N, dev, precision=prec)
@@ -861,18 +868,21 @@ def partition_section(torch, fnlh, inputs, dev, tol=1e-8, inner=12):
 
 
 def large_section(torch, fnlh, inputs, dev, tol=1e-8):
-    """c5: 256x200x156 (8M nodes), b=6, mean + 16 harmonics, BF16 blocks with FP64 defect correction;
+    """c5: 256x200x156 (8M nodes), b=6, mean + 16 harmonics, BF16 blocks with FP64 defect correction
+    (float-float intermediate checks, FP64 certifying check; the all-FP64-checks time beside it);
     Jacobian bytes for N=1 and N=16; peak device memory."""
     c = inputs.CONFIGS["c5"]
     mesh = inputs.hex_mesh(*c["dims"])
     q = inputs.flow_state(mesh.n_nodes, 6)
     n = mesh.n_nodes
     dm = fnlh.DeviceMesh.from_mesh(mesh, dev)
-    J = fnlh.DeviceJacobian(dm, 6, fnlh.FNLH_PREP_BF16, dev)
+    prep = fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF
+    J = fnlh.DeviceJacobian(dm, 6, prep, dev)
     fnlh.fnlh_build_jacobian(dm, torch.from_numpy(q).to(dev), fnlh.make_params(c["cfl"]), J)
     del q
     out = {"workload": f"c5: 256x200x156 hex passage, {n} nodes, {mesh.n_edges} edges, b=6, CFL {c['cfl']:g}, "
-                       f"BF16 blocks, FP64 defect correction to {tol:g}",
+                       f"BF16 blocks, FP64 defect correction to {tol:g} ({BF16_INNER} inner sweeps per correction, "
+                       f"float-float intermediate checks)",
            "jacobian_bytes": J.nbytes()}
     peaks, _ = load_peaks()
     for N in (16, 1):
@@ -881,16 +891,26 @@ def large_section(torch, fnlh, inputs, dev, tol=1e-8):
         B = torch.from_numpy(Bh).to(dev)
         del Bh
         X = torch.empty_like(B)
-        ws = fnlh.workspace(n, 6, N, dev, precision=fnlh.FNLH_BF16)
+        ws = fnlh.solve_workspace(n, 6, N, prep, dev, fnlh.FNLH_BF16)
         om = inputs.omegas(N)
         zg = fnlh.FNLH_SOLVE_ZERO_GUESS
-        fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 25, 1, ws=ws, raise_on_error=False, flags=zg)
+        fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, BF16_INNER, 1, ws=ws, raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, 25, 200, ws=ws,
+        st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, BF16_INNER, 200, ws=ws,
                                                   raise_on_error=False, flags=zg)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
+        peak = torch.cuda.max_memory_allocated(dev)
+        # the same solve with every check in FP64 (the plain workspace holds no float-float shadows)
+        ws64 = fnlh.workspace(n, 6, N, dev, precision=fnlh.FNLH_BF16)
+        t0 = time.perf_counter()
+        st64, checks64, sweeps64, rel64 = fnlh.fnlh_solve(dm, J, om, B, X, fnlh.FNLH_BF16, tol, BF16_INNER, 200,
+                                                          ws=ws64, raise_on_error=False, flags=zg)
+        torch.cuda.synchronize()
+        fp64_checks = {"seconds": time.perf_counter() - t0, "checks": checks64, "sweeps": sweeps64,
+                       "status": fnlh.fnlh_strerror(st64), "max_rel_residual": float(np.max(rel64))}
+        del ws64
 
         class _P:
             omega = om
@@ -902,7 +922,7 @@ def large_section(torch, fnlh, inputs, dev, tol=1e-8):
                         "updates_per_s": n * (1 + N) * sweeps / t,
                         "inner_sweep": {"ms": ms, "alg_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9,
                                         "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-                        "peak_device_bytes": torch.cuda.max_memory_allocated(dev)}
+                        "peak_device_bytes": peak, "fp64_checks": fp64_checks}
         del B, X, ws
         torch.cuda.empty_cache()
     out["jacobian_bytes_independent_of_N"] = out["N1"]["jacobian_bytes"] == out["N16"]["jacobian_bytes"]
@@ -981,7 +1001,7 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         sw = fn()
         torch.cuda.synchronize()
         solves[name] = {"seconds": time.perf_counter() - t0, "max_sweeps": sw}
-    for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, 25)):
+    for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, BF16_INNER)):
         sb = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
         sws = torch.empty(sb.workspace_bytes(6, pc), dtype=torch.uint8, device=dev)
         fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)

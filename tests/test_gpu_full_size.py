@@ -2,15 +2,18 @@
 configurations the benchmark times, checked by the oracle.
 
 * 160x128x102 passage (2,088,960 nodes), b = 6, mean + 8 harmonics: the
-  FP32-block (30 inner sweeps per FP64 residual) and BF16-block (25 inner)
-  defect-correction solves reach a true FP64 residual of 1e-8 per system, and
-  the residual the library reports agrees with the oracle's.
+  FP32-block (30 inner sweeps per correction) and BF16-block (21 inner)
+  defect-correction solves -- float-float intermediate checks, as the
+  benchmark times them, and all-FP64 checks -- reach a true FP64 residual of
+  1e-8 per system, and the residual the library reports agrees with the
+  oracle's.
 * Three blade rows (200,000 / 600,000 / 1,100,000 nodes, N = 2 / 8 / 4):
   20 batched FP64 sweeps match the oracle's Jacobi per row to 1e-12; the
   batched BF16 sweeps equal the per-row BF16 sweeps bit for bit; the
-  batched FP32 solve reaches 1e-8 on every row.
-* 256x200x156 passage (7,987,200 nodes), mean + 1 harmonic: the BF16 solve
-  reaches a true FP64 residual of 1e-8.
+  batched FP32 and BF16 solves reach 1e-8 on every row.
+* 256x200x156 passage (7,987,200 nodes), mean + 16 and mean + 1 harmonic:
+  the BF16 solves as the benchmark times them (21 inner sweeps, float-float
+  intermediate checks) reach a true FP64 residual of 1e-8.
 """
 
 import numpy as np
@@ -24,6 +27,9 @@ from tests import _gpu
 pytestmark = pytest.mark.gpu
 
 ZG = fnlh.FNLH_SOLVE_ZERO_GUESS
+C3_PREP = fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF
+C5_PREP = fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF
+BF16_INNER = 21  # the benchmark's inner sweeps per correction for BF16 blocks (FP32 blocks: 30)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,7 +41,7 @@ def _cuda():
 @pytest.fixture(scope="module")
 def passage_c3():
     p = inputs.config_problem("c3")
-    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16)
+    dm, J, B = _gpu.device_problem(p, prep_flags=C3_PREP)
     oj = _gpu.oracle_jacobian(p)
     yield p, dm, J, B, oj
     del dm, J, B
@@ -50,11 +56,14 @@ def check_true_residual(oj, p, X, rel_gpu, tol=1e-8):
     assert np.allclose(rel_gpu, true_rel, rtol=1e-6, atol=1e-12), (rel_gpu, true_rel)
 
 
-@pytest.mark.parametrize("prec,inner", [(fnlh.FNLH_F32, 30), (fnlh.FNLH_BF16, 25)])
-def test_passage_mixed_solve_full_size(passage_c3, prec, inner):
+@pytest.mark.parametrize("ff", [True, False])
+@pytest.mark.parametrize("prec,inner", [(fnlh.FNLH_F32, 30), (fnlh.FNLH_BF16, BF16_INNER)])
+def test_passage_mixed_solve_full_size(passage_c3, prec, inner, ff):
     p, dm, J, B, oj = passage_c3
     X = torch.zeros_like(B)
-    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=prec)
+    n = p.mesh.n_nodes
+    ws = (fnlh.solve_workspace(n, p.block, p.n_harm, C3_PREP, "cuda", prec) if ff
+          else fnlh.workspace(n, p.block, p.n_harm, "cuda", precision=prec))
     st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, inner, 200, ws=ws, flags=ZG)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     check_true_residual(oj, p, X, rel)
@@ -88,28 +97,30 @@ def test_blade_rows_batched_full_size():
     fnlh.fnlh_relax_batched(batch, 20, fnlh.FNLH_BF16, ws=ws)
     for X, ref in zip(Xs, singles):
         assert torch.equal(X, ref)
-    # the mixed batched solve reaches 1e-8 on every row
-    for X in Xs:
-        X.zero_()
+    # the mixed batched solves the benchmark times reach 1e-8 on every row
     del ws
-    sws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32), dtype=torch.uint8, device="cuda")
-    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F32, 1e-8, 30, 200, ws=sws, flags=ZG)
-    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
-    for p, X in zip(rows, Xs):
-        oj = _gpu.oracle_jacobian(p)
-        true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
-        assert np.all(true_rel <= 1e-8), (p.name, true_rel)
+    ojs = [_gpu.oracle_jacobian(p) for p in rows]
+    for prec, inner in ((fnlh.FNLH_F32, 30), (fnlh.FNLH_BF16, BF16_INNER)):
+        for X in Xs:
+            X.zero_()
+        sws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+        st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 1e-8, inner, 200, ws=sws, flags=ZG)
+        assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (prec, st, rel)
+        del sws
+        for p, X, oj in zip(rows, Xs, ojs):
+            true_rel = oracle.rel_residuals(oj, p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+            assert np.all(true_rel <= 1e-8), (prec, p.name, true_rel)
 
 
 def test_large_passage_bf16_solve_full_size():
     c = inputs.CONFIGS["c5"]
     p = inputs.config_problem("c5", n_harm=1)
     assert p.mesh.n_nodes == 7987200 and tuple(c["dims"]) == (256, 200, 156)
-    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_BF16)
+    dm, J, B = _gpu.device_problem(p, prep_flags=C5_PREP)
     X = torch.zeros_like(B)
-    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=fnlh.FNLH_BF16)
-    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, 25, 200, ws=ws,
-                                              flags=ZG)
+    ws = fnlh.solve_workspace(p.mesh.n_nodes, p.block, p.n_harm, C5_PREP, "cuda", fnlh.FNLH_BF16)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, BF16_INNER, 200,
+                                              ws=ws, flags=ZG)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     x = X.cpu().numpy()
     del dm, J, B, X, ws
@@ -122,18 +133,19 @@ def test_large_passage_bf16_solve_full_size():
 
 def test_large_passage_bf16_solve_n16_full_size():
     """The large case exactly as the benchmark times it: 256x200x156 (7,987,200
-    nodes), mean + 16 harmonics, BF16 blocks, 25 inner sweeps per FP64
-    residual, from zero to 1e-8.  The oracle's residual on the returned x
+    nodes), mean + 16 harmonics, BF16 blocks, 21 inner sweeps per correction,
+    float-float intermediate checks and an FP64 certifying check, from zero
+    to 1e-8.  The oracle's residual on the returned x
     (about 40 GB of host arrays: its FP64 Jacobian, B and x) certifies every
     one of the 17 systems at 1e-8 and agrees with the residual the library
     reports."""
     p = inputs.config_problem("c5")
     assert p.mesh.n_nodes == 7987200 and p.n_harm == 16
-    dm, J, B = _gpu.device_problem(p, prep_flags=fnlh.FNLH_PREP_BF16)
+    dm, J, B = _gpu.device_problem(p, prep_flags=C5_PREP)
     X = torch.empty_like(B)
-    ws = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, "cuda", precision=fnlh.FNLH_BF16)
-    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, 25, 200, ws=ws,
-                                              flags=ZG)
+    ws = fnlh.solve_workspace(p.mesh.n_nodes, p.block, p.n_harm, C5_PREP, "cuda", fnlh.FNLH_BF16)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_BF16, 1e-8, BF16_INNER, 200,
+                                              ws=ws, flags=ZG)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     x = X.cpu().numpy()
     del dm, J, B, X, ws
