@@ -937,7 +937,8 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         c = inputs.CONFIGS[key]
         p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=key)
         dm = fnlh.DeviceMesh.from_mesh(p.mesh, dev)
-        J = fnlh.DeviceJacobian(dm, p.block, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16, dev)
+        J = fnlh.DeviceJacobian(dm, p.block, fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
+                                | fnlh.FNLH_PREP_FF, dev)
         fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).to(dev), fnlh.make_params(p.cfl), J)
         B = torch.from_numpy(p.b).to(dev)
         rows.append((p, dm, J, B, torch.zeros_like(B),
@@ -1003,17 +1004,25 @@ def batched_section(torch, fnlh, inputs, dev, args, sweeps=20, prec_name="bf16")
         solves[name] = {"seconds": time.perf_counter() - t0, "max_sweeps": sw}
     for pname, pc, inner in (("f32", fnlh.FNLH_F32, 30), ("bf16", fnlh.FNLH_BF16, BF16_INNER)):
         sb = fnlh.BatchedRows([(dm, J, p.omega, B, X) for p, dm, J, B, X, ws in rows])
-        sws = torch.empty(sb.workspace_bytes(6, pc), dtype=torch.uint8, device=dev)
-        fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, c, sw, rel = fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        solves[f"batched_{pname}"] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": c, "sweeps": sw,
-                                      "max_rel_residual": float(np.max(rel)),
-                                      "speedup_vs_fp64_per_row": solves["fp64_per_row"]["seconds"] / t}
-        del sws
+        entry = {}
+        for ff in (True, False):  # float-float intermediate checks (the headline), then every check in FP64
+            sws = torch.empty(sb.workspace_bytes(6, pc, ff=ff), dtype=torch.uint8, device=dev)
+            fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg, raise_on_error=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, c, sw, rel = fnlh.fnlh_solve_batched(sb, pc, 1e-8, inner, 200, ws=sws, flags=zg,
+                                                     raise_on_error=False)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            res = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": c, "sweeps": sw,
+                   "max_rel_residual": float(np.max(rel))}
+            if ff:
+                entry = dict(res, inner_sweeps=inner,
+                             speedup_vs_fp64_per_row=solves["fp64_per_row"]["seconds"] / t)
+            else:
+                entry["fp64_checks"] = res
+            del sws
+        solves[f"batched_{pname}"] = entry
     return {"workload": "c4: rows 80x50x50 (N=2), 100x75x80 (N=8), 125x110x80 (N=4), b=6, "
                         f"{sweeps} {prec_name} sweeps", "per_row_ms": t_rows, "batched_ms": t_batch,
             "solve_to_1e-8": solves,

@@ -312,7 +312,11 @@ size_t fnlh_batched_extra_bytes(int32_t n_rows);
  * launches over all rows from e = 0, then x += Q e per row.  flags, outputs
  * and errors as fnlh_solve; rel_res (host, nullable) holds the rows' systems
  * one row after the other.  workspace as fnlh_relax_batched, with each row's
- * fnlh_workspace_bytes taken at `precision`.  SYNCHRONISING. */
+ * fnlh_workspace_bytes taken at `precision`.  When every row's prep blob has
+ * FNLH_PREP_FF, no row has periodic edges and the workspace holds the sum of
+ * the rows' fnlh_solve_workspace_bytes plus fnlh_batched_extra_bytes, the
+ * intermediate checks of a mixed solve run in float-float as in fnlh_solve
+ * (the check that ends the solve is FP64).  SYNCHRONISING. */
 int fnlh_solve_batched(const fnlh_row *rows, int32_t n_rows, int32_t precision, double tol,
                        int32_t inner_sweeps, int32_t max_checks, int32_t flags, const fnlh_tuning *tuning,
                        void *workspace, size_t workspace_bytes, int32_t *checks_done, int32_t *sweeps_done,

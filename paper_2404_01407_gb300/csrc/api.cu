@@ -22,8 +22,8 @@ int residual_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, cons
                     float*, const float*, int, double*, void*, cudaStream_t);
 Systems make_systems(int n_harm, const double* omega, const double* sigma);
 int batched_impl(const fnlh_row*, int, int, int, const fnlh_tuning*, void*, size_t, cudaStream_t);
-int solve_batched_impl(const fnlh_row*, int, int, double, int, int, int, const fnlh_tuning*, void*, int*, int*, double*,
-                       cudaStream_t);
+int solve_batched_impl(const fnlh_row*, int, int, double, int, int, int, const fnlh_tuning*, void*, size_t, int*, int*,
+                       double*, cudaStream_t);
 size_t batched_extra_bytes(int n_rows);
 void set_sweep_events(cudaEvent_t b, cudaEvent_t e);
 int residual_noalloc_launch(const fnlh_mesh*, const fnlh_jacobian*, const Systems&, const double*, const double*,
@@ -331,7 +331,7 @@ int fnlh_solve_batched(const fnlh_row* rows, int32_t n_rows, int32_t precision, 
   if (!aligned(workspace, 256)) return FNLH_ERR_ARG;
   if (workspace_bytes < need) return FNLH_ERR_WORKSPACE;
   return solve_batched_impl(rows, n_rows, precision, tol, inner_sweeps, max_checks, flags, tuning, workspace,
-                            checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
+                            workspace_bytes, checks_done, sweeps_done, rel_res, (cudaStream_t)stream);
 }
 
 int fnlh_residual_noalloc(const fnlh_mesh* mesh, const fnlh_jacobian* J, int32_t n_harm, const double* omega,

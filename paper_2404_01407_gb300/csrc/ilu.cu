@@ -48,7 +48,8 @@ int residual_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& s
 Systems make_systems(int n_harm, const double* omega, const double* sigma);
 int mark_sweeps_begin(cudaStream_t s);
 int mark_sweeps_end(cudaStream_t s);
-int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s);
+int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s,
+               float2* xff = nullptr);
 
 // ------------------------------------------------------------- validation
 

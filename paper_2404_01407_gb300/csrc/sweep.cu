@@ -524,11 +524,15 @@ static inline int mark(cudaEvent_t ev, cudaStream_t s) {
 }
 
 // x += Q e with the product in FP32 and the sum in FP64 (csrc/ilu.cu).
-int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s) {
+int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s,
+               float2* xff = nullptr);
+
+// xff (nullable): the float-float shadow of X, advanced by the same correction.
+int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s, float2* xff) {
   const long long count = (long long)n * K;
   if (count == 0) return FNLH_OK;
-  if (BS == 5) k_update_f32<5><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X);
-  else k_update_f32<6><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X);
+  if (BS == 5) k_update_f32<5><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X, xff);
+  else k_update_f32<6><<<blocks_for(count, 256), 256, 0, s>>>(count, K, rotf, e, X, xff);
   FNLH_LAUNCH_CHECK();
   return FNLH_OK;
 }
@@ -926,9 +930,11 @@ struct BatchPlan {
   int n_rows;
 };
 
+// ff_layout: each row's workspace slice also holds the float-float shadows
+// of B and x (ws_layout total_ff instead of total).
 template <int BS, typename TJ, typename T>
 int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuning* tn, void* ws, BatchArgs& a,
-                BatchPlan& P) {
+                BatchPlan& P, bool ff_layout = false) {
   std::memset(&a, 0, sizeof(a));
   P.threads = (tn && tn->threads > 0) ? tn->threads : (sizeof(T) == 4 ? kSweepThreadsF32 : kSweepThreads);
   const int ctas_per_sm = tn ? tn->ctas_per_sm : 0;  // 0: one CTA per tile
@@ -951,7 +957,7 @@ int batch_setup(const fnlh_row* rows, int n_rows, int precision, const fnlh_tuni
     const WsLayout W = ws_layout(R.mesh->n_nodes, BS, R.n_harm, precision);
     char* base = (char*)ws + off;
     P.base[r] = base;
-    off += W.total;
+    off += ff_layout ? W.total_ff : W.total;
     BatchRow& D = a.row[r];
     D.row.n = R.mesh->n_nodes;
     D.row.K = sys.K;
@@ -1143,13 +1149,27 @@ int batched_typed(const fnlh_row* rows, int n_rows, int sweeps, int precision, c
 // batched launch per inner sweep from e = 0 over all rows, x += Q e).
 template <int BS, typename TJ, typename T>
 int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double tol, int inner, int max_checks,
-                        int flags, const fnlh_tuning* tn, void* ws, int* checks_done, int* sweeps_done,
-                        double* rel_res, cudaStream_t s) {
+                        int flags, const fnlh_tuning* tn, void* ws, size_t ws_bytes, int* checks_done,
+                        int* sweeps_done, double* rel_res, cudaStream_t s) {
   BatchArgs& a = g_batch;
   BatchPlan P;
-  int rc = batch_setup<BS, TJ, T>(rows, n_rows, precision, tn, ws, a, P);
-  if (rc) return rc;
   const bool mixed = sizeof(T) == 4;
+  // Float-float checks, as in fnlh_solve: every row's prep blob has the split
+  // blocks (FNLH_PREP_FF), no row has periodic edges, and the workspace holds
+  // every row's shadows of B and x.
+  bool ff = mixed;
+  {
+    size_t need = batched_extra_bytes(n_rows);
+    for (int r = 0; r < n_rows && ff; ++r) {
+      const fnlh_jacobian* J = rows[r].J;
+      const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
+      if (PL.offdff == (size_t)-1 || rows[r].mesh->periodic != nullptr || J->n_nodes == 0) ff = false;
+      need += ws_layout(J->n_nodes, BS, rows[r].n_harm, precision).total_ff;
+    }
+    ff = ff && ws_bytes >= need;
+  }
+  int rc = batch_setup<BS, TJ, T>(rows, n_rows, precision, tn, ws, a, P, ff);
+  if (rc) return rc;
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
   const bool per_row = per_row_mode(tn);
@@ -1170,36 +1190,84 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
       if ((rc = rotate_in<BS, T>(D.row.n, D.row.K, P.ops[r].rot, rows[r].X, (T*)D.x[0], s))) return rc;
     }
   }
+  float2* bff[kMaxBatchRows] = {};
+  float2* xff[kMaxBatchRows] = {};
+  if (ff)
+    for (int r = 0; r < n_rows; ++r) {
+      const WsLayout W = ws_layout(a.row[r].row.n, BS, a.row[r].row.K - 1, precision);
+      bff[r] = at<float2>(P.base[r], W.bff);
+      xff[r] = at<float2>(P.base[r], W.xff);
+      const long long nv = (long long)a.row[r].row.n * P.sys[r].C * BS;
+      k_split_vec<<<blocks_for(nv, 256), 256, 0, s>>>(nv, rows[r].B, bff[r]);
+      FNLH_LAUNCH_CHECK();
+      if (x_zero) {
+        FNLH_CUDA_TRY(cudaMemsetAsync(xff[r], 0, sizeof(float2) * (size_t)nv, s));
+      } else {
+        k_split_vec<<<blocks_for(nv, 256), 256, 0, s>>>(nv, rows[r].X, xff[r]);
+        FNLH_LAUNCH_CHECK();
+      }
+    }
   a.parity = 0;
   std::vector<double> hn(2 * kMaxSys * n_rows);
   std::vector<double> rel(kMaxSys * n_rows, 0.0);
-  double first_max = 0.0;
+  std::vector<double> bnorm(kMaxSys * n_rows, 0.0);  // ||B_k||^2 per row and system, from the first (FP64) check
+  double first_max = 0.0, prev_worst = -1.0;
+  bool fp64_next = false;
   int checks = 0, sweeps = 0;
   bool conv = false;
-  for (;;) {
-    for (int r = 0; r < n_rows; ++r) {
-      const BatchRow& D = a.row[r];
-      const WsLayout W = ws_layout(D.row.n, BS, D.row.K - 1, precision);
-      double* norms = at<double>(P.base[r], W.norms);
-      rc = residual_launch(rows[r].mesh, rows[r].J, P.sys[r], rows[r].B, rows[r].X, nullptr,
-                           mixed ? (float*)D.row.Bt : nullptr, P.ops[r].rotf, x_zero ? 1 : 0, norms, P.base[r], s);
-      if (rc) return rc;
-      FNLH_CUDA_TRY(cudaMemcpyAsync(hn.data() + 2 * kMaxSys * r, norms, sizeof(double) * 2 * D.row.K,
-                                    cudaMemcpyDeviceToHost, s));
-    }
-    x_zero = false;
-    FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+  // the relative residuals of hn into rel; returns the worst, or -1 on a non-finite value
+  auto evaluate = [&]() -> double {
     double worst = 0.0;
-    bool finite = true;
     for (int r = 0; r < n_rows; ++r)
       for (int k = 0; k < a.row[r].row.K; ++k) {
         const double rr = hn[2 * kMaxSys * r + 2 * k], bb = hn[2 * kMaxSys * r + 2 * k + 1];
-        if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) finite = false;
+        if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) return -1.0;
         const double v = (bb > 0.0) ? std::sqrt(rr / bb) : std::sqrt(rr);
         rel[kMaxSys * r + k] = v;
         worst = std::max(worst, v);
       }
-    if (!finite) {
+    return worst;
+  };
+  for (;;) {
+    // float-float check of every row; a passing one is confirmed at once in FP64
+    bool need64 = true;
+    if (ff && checks > 0 && !fp64_next) {
+      for (int r = 0; r < n_rows; ++r) {
+        const BatchRow& D = a.row[r];
+        const WsLayout W = ws_layout(D.row.n, BS, D.row.K - 1, precision);
+        double* norms = at<double>(P.base[r], W.norms);
+        rc = residual_ff_launch(rows[r].mesh, rows[r].J, P.sys[r], bff[r], xff[r], (float*)D.row.Bt,
+                                P.ops[r].rotf, norms, P.base[r], s);
+        if (rc) return rc;
+        FNLH_CUDA_TRY(cudaMemcpyAsync(hn.data() + 2 * kMaxSys * r, norms, sizeof(double) * 2 * D.row.K,
+                                      cudaMemcpyDeviceToHost, s));
+      }
+      FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int r = 0; r < n_rows; ++r)
+        for (int k = 0; k < a.row[r].row.K; ++k) hn[2 * kMaxSys * r + 2 * k + 1] = bnorm[kMaxSys * r + k];
+      const double w = evaluate();
+      need64 = !(w >= 0.0) || w <= tol;
+    }
+    if (need64) {
+      for (int r = 0; r < n_rows; ++r) {
+        const BatchRow& D = a.row[r];
+        const WsLayout W = ws_layout(D.row.n, BS, D.row.K - 1, precision);
+        double* norms = at<double>(P.base[r], W.norms);
+        rc = residual_launch(rows[r].mesh, rows[r].J, P.sys[r], rows[r].B, rows[r].X, nullptr,
+                             mixed ? (float*)D.row.Bt : nullptr, P.ops[r].rotf, x_zero ? 1 : 0, norms, P.base[r],
+                             s);
+        if (rc) return rc;
+        FNLH_CUDA_TRY(cudaMemcpyAsync(hn.data() + 2 * kMaxSys * r, norms, sizeof(double) * 2 * D.row.K,
+                                      cudaMemcpyDeviceToHost, s));
+      }
+      x_zero = false;
+      FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+      if (checks == 0)
+        for (int r = 0; r < n_rows; ++r)
+          for (int k = 0; k < a.row[r].row.K; ++k) bnorm[kMaxSys * r + k] = hn[2 * kMaxSys * r + 2 * k + 1];
+    }
+    const double worst = evaluate();
+    if (!(worst >= 0.0)) {
       rc = FNLH_ERR_NONFINITE;
       break;
     }
@@ -1211,6 +1279,10 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
     ++checks;
     conv = worst <= tol;
     if (conv || checks >= max_checks) break;
+    if (ff) {  // does the decay predict the next check at or below 2 tol?  Then make it in FP64.
+      fp64_next = prev_worst > 0.0 && worst * worst / prev_worst <= 2.0 * tol;
+      prev_worst = worst;
+    }
     if (masking)  // converged systems are frozen for the following sweeps
       for (int r = 0; r < n_rows; ++r) {
         BatchRow& D = a.row[r];
@@ -1225,7 +1297,8 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
       if (rc) return rc;
       for (int r = 0; r < n_rows; ++r) {
         const BatchRow& D = a.row[r];
-        if ((rc = update_f32(D.row.n, D.row.K, BS, P.ops[r].rotf, (const float*)D.x[a.parity], rows[r].X, s)))
+        if ((rc = update_f32(D.row.n, D.row.K, BS, P.ops[r].rotf, (const float*)D.x[a.parity], rows[r].X, s,
+                             xff[r])))
           return rc;
       }
     } else {
@@ -1252,15 +1325,15 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
 }
 
 int solve_batched_impl(const fnlh_row* rows, int n_rows, int precision, double tol, int inner, int max_checks,
-                       int flags, const fnlh_tuning* tn, void* ws, int* checks_done, int* sweeps_done, double* rel_res,
-                       cudaStream_t s) {
+                       int flags, const fnlh_tuning* tn, void* ws, size_t ws_bytes, int* checks_done,
+                       int* sweeps_done, double* rel_res, cudaStream_t s) {
   if (n_rows > kMaxBatchRows) return FNLH_ERR_UNSUPPORTED;
   const int b = rows[0].J->block;
   for (int r = 1; r < n_rows; ++r)
     if (rows[r].J->block != b) return FNLH_ERR_UNSUPPORTED;
 #define FNLH_SB(BS, TJ, T) \
-  solve_batched_typed<BS, TJ, T>(rows, n_rows, precision, tol, inner, max_checks, flags, tn, ws, checks_done, \
-                                 sweeps_done, rel_res, s)
+  solve_batched_typed<BS, TJ, T>(rows, n_rows, precision, tol, inner, max_checks, flags, tn, ws, ws_bytes, \
+                                 checks_done, sweeps_done, rel_res, s)
   if (b == 5) {
     if (precision == FNLH_F64) return FNLH_SB(5, double, double);
     if (precision == FNLH_F32) return FNLH_SB(5, float, float);

@@ -381,10 +381,17 @@ class BatchedRows:
         self.arr = arr
         self.n = len(rows)
 
-    def workspace_bytes(self, block, precision=FNLH_F64):
+    def workspace_bytes(self, block, precision=FNLH_F64, ff=False):
+        """Workspace of fnlh_relax_batched / fnlh_solve_batched; ff=True adds every row's float-float
+        shadows (fnlh_solve_workspace_bytes), which the batched mixed solve uses when every row's
+        Jacobian has FNLH_PREP_FF."""
         total = int(lib().fnlh_batched_extra_bytes(self.n))
         for dm, J, om, B, X in self.keep:
-            total += fnlh_workspace_bytes(dm.n_nodes, block, (B.shape[1] - 1) // 2, precision)
+            nh = (B.shape[1] - 1) // 2
+            if ff:
+                total += fnlh_solve_workspace_bytes(dm.n_nodes, block, nh, precision, J.c.prep_flags)
+            else:
+                total += fnlh_workspace_bytes(dm.n_nodes, block, nh, precision)
         return total
 
 

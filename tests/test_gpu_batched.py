@@ -199,3 +199,81 @@ def test_per_row_mode_equals_single_row_calls(prec):
     assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks and sw == inner * (checks - 1)
     for X, ref in zip(Xs, solos):
         assert torch.equal(X, ref)
+
+
+FF_PREP = _gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS | fnlh.FNLH_PREP_FF
+
+
+def device_rows_ff(probs, prep=FF_PREP):
+    dev = []
+    for p in probs:
+        dm = fnlh.DeviceMesh.from_mesh(p.mesh, "cuda")
+        J = fnlh.DeviceJacobian(dm, p.block, prep)
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).cuda(), fnlh.make_params(p.cfl), J)
+        dev.append((p, dm, J, torch.from_numpy(p.b).cuda()))
+    return dev
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_batched_float_float_solve_equals_per_row(prec):
+    """tol = 0: every check after the first is float-float in both, so the
+    batched solve makes the per-row solves' corrections, bit for bit."""
+    dev = device_rows_ff(rows_problem())
+    inner, checks = 6, 4
+    singles = []
+    for p, dm, J, B in dev:
+        X = torch.zeros_like(B)
+        ws = fnlh.solve_workspace(p.mesh.n_nodes, 6, p.n_harm, FF_PREP, "cuda", prec)
+        st, c, sw, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 0.0, inner, checks, ws=ws,
+                                         raise_on_error=False)
+        assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks
+        singles.append((X, rel))
+    Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, prec, ff=True), dtype=torch.uint8, device="cuda")
+    assert ws.numel() > batch.workspace_bytes(6, prec)
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 0.0, inner, checks, ws=ws, raise_on_error=False)
+    assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == checks and sw == inner * (checks - 1)
+    o = 0
+    for X, (ref, rel1), (p, *_r) in zip(Xs, singles, dev):
+        assert torch.equal(X, ref)
+        assert np.array_equal(rel[o:o + 1 + p.n_harm], rel1)
+        o += 1 + p.n_harm
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+@pytest.mark.parametrize("flags", [0, fnlh.FNLH_SOLVE_MASK_CONVERGED])
+def test_batched_float_float_solve_certified_by_oracle(prec, flags):
+    probs = rows_problem()
+    dev = device_rows_ff(probs)
+    Xs = [torch.full_like(B, 3.0) for (_, _, _, B) in dev]
+    batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+    ws = torch.empty(batch.workspace_bytes(6, prec, ff=True), dtype=torch.uint8, device="cuda")
+    st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 1e-8, 12, 60, ws=ws,
+                                             flags=flags | fnlh.FNLH_SOLVE_ZERO_GUESS)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    o = 0
+    for p, X in zip(probs, Xs):
+        true_rel = oracle.rel_residuals(_gpu.oracle_jacobian(p), p.mesh.vol, p.omega, p.b, X.cpu().numpy())
+        assert np.all(true_rel <= 1e-8), true_rel
+        # the reported residuals are the certifying FP64 check's
+        assert np.allclose(rel[o:o + 1 + p.n_harm], true_rel, rtol=1e-6, atol=1e-12)
+        o += 1 + p.n_harm
+
+
+def test_batched_float_float_needs_every_row_split():
+    """One row without FNLH_PREP_FF: the batch takes every check in FP64, as
+    with the plain workspace, whatever the workspace size."""
+    probs = rows_problem()
+    dev = device_rows_ff(probs[:2]) + device_rows_ff(probs[2:], prep=_gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS)
+    out = []
+    for ff in (True, False):
+        Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
+        batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
+        ws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32, ff=ff), dtype=torch.uint8, device="cuda")
+        st, c, sw, rel = fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F32, 0.0, 6, 3, ws=ws, raise_on_error=False)
+        assert st == fnlh.FNLH_ERR_NOT_CONVERGED and c == 3
+        out.append((Xs, rel))
+    for Xa, Xb in zip(out[0][0], out[1][0]):
+        assert torch.equal(Xa, Xb)
+    assert np.array_equal(out[0][1], out[1][1])
