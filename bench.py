@@ -53,8 +53,8 @@ BF16_INNER = 21  # BF16-block inner sweeps per correction (FP32 blocks: 30)
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of the top kernel from an ncu capture (profiles/k_sweep_f64_c2.md),
 # valid only while the kernel's sources hash to the value they had when it was taken
-NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363046144 + 177946880,
-                                  "sources_sha256": "70601bfd3d4cd853baa780f7648ca6b374fbe65f2bf1b83bc196f56014d3695f"}}
+NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363066112 + 178004480,
+                                  "sources_sha256": "92bc737572c1942a78205fbce66b21711dc8e13f647de585d8309f2b415378da"}}
 KERNEL_SOURCES = ("paper_2404_01407_gb300/csrc/sweep.cu", "paper_2404_01407_gb300/csrc/sweep_kernel.cuh",
                   "paper_2404_01407_gb300/csrc/common.cuh", "include/fnlh.h")
 
