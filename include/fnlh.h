@@ -407,7 +407,10 @@ int fnlh_ilu_factor(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_har
  * paper's rule).  flags: FNLH_SOLVE_ZERO_GUESS, FNLH_SOLVE_MASK_CONVERGED.
  * SYNCHRONISING.  Outputs (host, nullable): *iterations_done, rel_res [K].
  * Returns FNLH_ERR_NOT_CONVERGED after max_iterations, FNLH_ERR_NONFINITE /
- * FNLH_ERR_DIVERGED as fnlh_solve.  workspace: the FNLH_F64 size. */
+ * FNLH_ERR_DIVERGED as fnlh_solve.  workspace: the FNLH_F64 size.  With an
+ * FP32 factor and FNLH_PREP_FF in J's prep (no periodic edges), the residual
+ * of every iteration after the first is taken in float-float as in
+ * fnlh_solve, and the one that ends the solve in FP64. */
 int fnlh_solve_ilu(const fnlh_mesh *mesh, const fnlh_jacobian *J, const fnlh_ilu *ilu, int32_t n_harm,
                    const double *omega, const double *sigma, const double *B, double *X, double tol,
                    int32_t max_iterations, int32_t flags, void *workspace, size_t workspace_bytes,

@@ -50,6 +50,9 @@ int mark_sweeps_begin(cudaStream_t s);
 int mark_sweeps_end(cudaStream_t s);
 int update_f32(int n, int K, int BS, const float* rotf, const float* e, double* X, cudaStream_t s,
                float2* xff = nullptr);
+int residual_ff_launch(const fnlh_mesh* m, const fnlh_jacobian* J, const Systems& sys, const float2* bff,
+                       const float2* xff, float* r32rot, const float* rotf, double* norms, void* ws, cudaStream_t s);
+int split_ff(long long count, const double* v, float2* out, cudaStream_t s);
 
 // ------------------------------------------------------------- validation
 
@@ -587,28 +590,62 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
   if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
-  double hn[2 * kMaxSys];
+  // Float-float checks (FP32 smoother, prep blob with FNLH_PREP_FF, no periodic
+  // edges), as in fnlh_solve: every residual after the first on the FP32 units
+  // from float-float shadows of B and x, a passing one confirmed at once in
+  // FP64, and one that the decay predicts at or below 2 tol made in FP64
+  // directly.  The shadows take the workspace's third vector and pivot-table
+  // slots, which this solve does not use otherwise (each holds n C b float2).
+  const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
+  const bool ff = kRot && n > 0 && PL.offdff != (size_t)-1 && m->periodic == nullptr;
+  float2* bff = ff ? at<float2>(ws, W.vec[2]) : nullptr;
+  float2* xff = ff ? at<float2>(ws, W.pivinv) : nullptr;
+  int it = 0, rc = FNLH_OK;
+  if (ff) {
+    const long long nv = (long long)n * sys.C * BS;
+    if ((rc = split_ff(nv, B, bff, s))) return rc;
+    if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(xff, 0, sizeof(float2) * (size_t)nv, s));
+    else if ((rc = split_ff(nv, X, xff, s))) return rc;
+  }
+  double hn[2 * kMaxSys], bnorm[kMaxSys] = {};
   IluCheck ck;
   ck.first_max = 0.0;
-  int it = 0, rc = FNLH_OK;
-  bool conv = false;
-  for (;;) {
-    // FP64: r in the caller's layout; FP32: Q^T r in FP32 straight from the residual kernel
-    if ((rc = residual_launch(m, J, sys, B, X, kRot ? nullptr : r, kRot ? (float*)r : nullptr, rotf, x_zero ? 1 : 0,
-                              norms, ws, s)))
-      return rc;
-    x_zero = false;
-    FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
-    FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+  bool conv = false, fp64_next = false;
+  double prev_worst = -1.0;
+  // the relative residuals of hn into ck.rel; returns the worst, or -1 on a non-finite value
+  auto evaluate = [&]() -> double {
     double worst = 0.0;
-    bool finite = true;
     for (int k = 0; k < K; ++k) {
       const double rr = hn[2 * k], bb = hn[2 * k + 1];
-      if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) finite = false;
+      if (!(rr == rr) || !(bb == bb) || rr > 1e300 || bb > 1e300) return -1.0;
       ck.rel[k] = (bb > 0.0) ? std::sqrt(rr / bb) : std::sqrt(rr);
       worst = std::max(worst, ck.rel[k]);
     }
-    if (!finite) {
+    return worst;
+  };
+  for (;;) {
+    bool need64 = true;
+    if (ff && it > 0 && !fp64_next) {
+      if ((rc = residual_ff_launch(m, J, sys, bff, xff, (float*)r, rotf, norms, ws, s))) return rc;
+      FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
+      FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int k = 0; k < K; ++k) hn[2 * k + 1] = bnorm[k];
+      const double w = evaluate();
+      need64 = !(w >= 0.0) || w <= tol;
+    }
+    if (need64) {
+      // FP64: r in the caller's layout; FP32: Q^T r in FP32 straight from the residual kernel
+      if ((rc = residual_launch(m, J, sys, B, X, kRot ? nullptr : r, kRot ? (float*)r : nullptr, rotf,
+                                x_zero ? 1 : 0, norms, ws, s)))
+        return rc;
+      x_zero = false;
+      FNLH_CUDA_TRY(cudaMemcpyAsync(hn, norms, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
+      FNLH_CUDA_TRY(cudaStreamSynchronize(s));
+      if (it == 0)
+        for (int k = 0; k < K; ++k) bnorm[k] = hn[2 * k + 1];
+    }
+    const double worst = evaluate();
+    if (!(worst >= 0.0)) {
       rc = FNLH_ERR_NONFINITE;
       break;
     }
@@ -619,6 +656,10 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
     }
     conv = worst <= tol;
     if (conv || it >= max_iterations) break;
+    if (ff) {  // does the decay predict the next check at or below 2 tol?  Then make it in FP64.
+      fp64_next = prev_worst > 0.0 && worst * worst / prev_worst <= 2.0 * tol;
+      prev_worst = worst;
+    }
     if (masking) {
       a.masked = 1;
       for (int k = 0; k < K; ++k)
@@ -642,7 +683,7 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
       FNLH_LAUNCH_CHECK();
     }
     if ((rc = mark_sweeps_end(s))) return rc;
-    if (kRot && (rc = update_f32(n, K, BS, rotf, (const float*)a.E, X, s))) return rc;
+    if (kRot && (rc = update_f32(n, K, BS, rotf, (const float*)a.E, X, s, xff))) return rc;
     ++it;
   }
   if (iterations_done) *iterations_done = it;

@@ -392,6 +392,14 @@ __global__ void __launch_bounds__(256) k_split_vec(long long count, const double
   if (e < count) out[e] = ff_split(v[e]);
 }
 
+// Host side of k_split_vec (csrc/ilu.cu: the FP32 ILU(0) solve's float-float checks).
+int split_ff(long long count, const double* v, float2* out, cudaStream_t s) {
+  if (count <= 0) return FNLH_OK;
+  k_split_vec<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, v, out);
+  FNLH_LAUNCH_CHECK();
+  return FNLH_OK;
+}
+
 static inline unsigned blocks_for(long long count, int threads) {
   return (unsigned)((count + threads - 1) / threads);
 }

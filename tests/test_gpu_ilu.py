@@ -170,3 +170,31 @@ def test_ilu_larger_passage_matches_oracle():
     run_iterations(dm, J, ilu, p, B, X, 3)
     ref = oracle.ilu_iterate(oj, p.mesh.vol, p.omega, p.b, 3, ilu.color_host)
     _gpu.assert_fp64_parity(X.cpu().numpy(), ref, p.n_harm)
+
+
+def test_ilu_f32_float_float_checks():
+    """FP32 factor with FNLH_PREP_FF: the residual of every iteration after
+    the first is float-float (the one that ends the solve FP64), so the solve
+    takes the same iterations as with FP64 residuals, its corrections agree to
+    rounding, and the oracle certifies the 1e-8."""
+    p = inputs.problem((24, 16, 12), 6, 4, 20.0)
+    m = p.mesh
+    out = {}
+    for ff in (False, True):
+        dm = fnlh.DeviceMesh.from_mesh(m, "cuda")
+        J = fnlh.DeviceJacobian(dm, p.block, PREP | (fnlh.FNLH_PREP_FF if ff else 0))
+        fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).cuda(), fnlh.make_params(p.cfl), J)
+        ilu = fnlh.DeviceIlu(dm, p.block, p.n_harm, precision=fnlh.FNLH_F32)
+        fnlh.fnlh_ilu_factor(dm, J, p.omega, ilu)
+        B = torch.from_numpy(p.b).cuda()
+        X = torch.zeros_like(B)
+        st, its, rel = fnlh.fnlh_solve_ilu(dm, J, ilu, p.omega, B, X, 1e-8, 100, flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
+        assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (ff, st, rel)
+        out[ff] = (its, X.cpu().numpy())
+    assert out[True][0] == out[False][0]
+    oj = oracle.build_jacobian(m.n_nodes, m.edge_nodes, m.normals, p.q, p.cfl)
+    true_rel = oracle.rel_residuals(oj, m.vol, p.omega, p.b, out[True][1])
+    assert np.all(true_rel <= 1e-8), true_rel
+    # the two runs differ only in the rounding of the intermediate residuals
+    err = _gpu.rel_err_per_system(out[True][1], out[False][1], p.n_harm)
+    assert np.all(err <= 1e-6), err
