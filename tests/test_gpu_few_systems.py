@@ -147,12 +147,14 @@ def test_few_systems_solve_certified_by_oracle(prec, flags, ff):
     assert np.all(true_rel <= 1e-8), true_rel
 
 
-def test_few_systems_ilu_f32_equals_leading_systems():
+@pytest.mark.parametrize("ff", [False, True])
+def test_few_systems_ilu_f32_equals_leading_systems(ff):
     """FP32 ILU(0): the correction vector of an N = 1 problem keeps the real
-    mean flow; fixed iterations give the N = 2 problem's first columns."""
+    mean flow; fixed iterations give the N = 2 problem's first columns (with
+    float-float residuals too: the residual writes the real mean flow)."""
     dims = (13, 6, 5)
     p = inputs.problem(dims, 6, 2, 20.0)
-    dm, J, B = device(p)
+    dm, J, B = device(p, prep=FF_PREP if ff else PREP)
     color = inputs.lattice_colors(dims)
     out = {}
     for nh in (2, 1, 0):
@@ -195,12 +197,15 @@ def test_batched_rows_with_few_systems_match_per_row(prec):
 
 @pytest.mark.parametrize("prec", LOW)
 @pytest.mark.parametrize("flags", [0, fnlh.FNLH_SOLVE_MASK_CONVERGED])
-def test_batched_solve_with_few_systems_certified_by_oracle(prec, flags):
+@pytest.mark.parametrize("ff", [False, True])
+def test_batched_solve_with_few_systems_certified_by_oracle(prec, flags, ff):
+    """With ff the rows' float-float shadows are in the workspace: the rows
+    of K <= 2 systems, swept by their own launches, advance theirs too."""
     probs = batch_rows()
-    dev = [(p, *device(p)) for p in probs]
+    dev = [(p, *device(p, prep=FF_PREP if ff else PREP)) for p in probs]
     Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
     batch = fnlh.BatchedRows([(dm, J, p.omega, B, X) for (p, dm, J, B), X in zip(dev, Xs)])
-    ws = torch.empty(batch.workspace_bytes(6, prec), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(batch.workspace_bytes(6, prec, ff=ff), dtype=torch.uint8, device="cuda")
     st, c, sw, rel = fnlh.fnlh_solve_batched(batch, prec, 1e-8, 12, 60, ws=ws, flags=flags)
     assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
     for p, X in zip(probs, Xs):
