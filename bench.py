@@ -53,8 +53,8 @@ BF16_INNER = 21  # BF16-block inner sweeps per correction (FP32 blocks: 30)
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of the top kernel from an ncu capture (profiles/k_sweep_f64_c2.md),
 # valid only while the kernel's sources hash to the value they had when it was taken
-NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363135744 + 177603840,
-                                  "sources_sha256": "a6e9c4b293647501f848c611894271b881573975d051e7374a39be34d57a59b7"}}
+NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363065344 + 177597696,
+                                  "sources_sha256": "b9b51d8dc2049f3eca1e03ca8f844eceaad11511cd4b81de555ca1b200f9d99b"}}
 KERNEL_SOURCES = ("paper_2404_01407_gb300/csrc/sweep.cu", "paper_2404_01407_gb300/csrc/sweep_kernel.cuh",
                   "paper_2404_01407_gb300/csrc/common.cuh", "include/fnlh.h")
 
@@ -689,10 +689,11 @@ def periodic_section(torch, fnlh, inputs, dev):
     """Phase-lagged periodic edges on the measured workload: the same passage
     with its pitchwise boundary closed by 6,144 periodic edges, harmonic l at
     inter-blade phase angle 2 pi l 3/8.  Sweep time per precision against the
-    same mesh without the closure, and the FP64 solve to a 1e-8 residual."""
+    same mesh without the closure, and the mixed FP32 solve to a 1e-8 FP64 residual (float-float
+    intermediate checks with the phase factors; the all-FP64-checks time beside it)."""
     c = inputs.CONFIGS[WORKLOAD]
     out = {}
-    prep = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16
+    prep = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_BF16 | fnlh.FNLH_PREP_FF
     for tag, periodic in (("plain", False), ("periodic", True)):
         p = inputs.problem(c["dims"], c["block"], c["n_harm"], c["cfl"], c["omega_base"], name=WORKLOAD,
                            periodic=periodic)
@@ -708,11 +709,25 @@ def periodic_section(torch, fnlh, inputs, dev):
         if periodic:
             out["workload"] = (f"{WORKLOAD} passage closed pitchwise by {int((p.mesh.periodic != 0).sum())} "
                                f"periodic edges, sigma_l = 2 pi l 3/8, l = 1..{p.n_harm}")
-            st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 12, 100, ws=ws,
-                                                      raise_on_error=False, flags=fnlh.FNLH_SOLVE_ZERO_GUESS,
-                                                      sigma=p.phase)
-            rec["mixed_f32_solve"] = {"status": fnlh.fnlh_strerror(st), "sweeps": sweeps,
-                                      "max_rel_residual": float(np.max(rel))}
+            def solve(w):
+                fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 12, 2, ws=w, raise_on_error=False,
+                                flags=fnlh.FNLH_SOLVE_ZERO_GUESS, sigma=p.phase)  # warm
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = fnlh.fnlh_solve(dm, J, p.omega, B, X, fnlh.FNLH_F32, 1e-8, 12, 100, ws=w,
+                                      raise_on_error=False, flags=fnlh.FNLH_SOLVE_ZERO_GUESS, sigma=p.phase)
+                torch.cuda.synchronize()
+                return time.perf_counter() - t0, res
+
+            # the FP64-sized workspace holds the float-float shadows; the plain FP32 one does not
+            t, (st, checks, sweeps, rel) = solve(ws)
+            ws32 = fnlh.workspace(p.mesh.n_nodes, p.block, p.n_harm, dev, precision=fnlh.FNLH_F32)
+            t64, (st64, checks64, sweeps64, rel64) = solve(ws32)
+            del ws32
+            rec["mixed_f32_solve"] = {"status": fnlh.fnlh_strerror(st), "seconds": t, "checks": checks,
+                                      "sweeps": sweeps, "max_rel_residual": float(np.max(rel)),
+                                      "fp64_checks": {"seconds": t64, "checks": checks64, "sweeps": sweeps64,
+                                                      "max_rel_residual": float(np.max(rel64))}}
         out[tag] = rec
         del dm, J, B, X, ws
         torch.cuda.empty_cache()

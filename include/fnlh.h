@@ -272,8 +272,9 @@ size_t fnlh_solve_workspace_bytes(int32_t n_nodes, int32_t block, int32_t n_harm
  * or confirmed, with the FP64 residual before the solve reports convergence:
  * a float-float check at tol is followed at once by an FP64 one, and when the
  * residual's decay (the last two checks' ratio) predicts the next check at
- * or below 2 tol, the next check is FP64 directly.  Meshes with `periodic`
- * keep FP64 checks.
+ * or below 2 tol, the next check is FP64 directly.  On a mesh with
+ * `periodic` the float-float residual applies the phase factor of Eq.
+ * lhs_lin to the product of each periodic entry (FNLH_PREP_TAGS as usual).
  * On a mesh with `part` the FP64 solve is a defect
  * correction too (inner FP64 sweeps without the cross-partition couplings,
  * FP64 residual with them).  X: in x0 (ignored with FNLH_SOLVE_ZERO_GUESS), out x.
@@ -313,7 +314,7 @@ size_t fnlh_batched_extra_bytes(int32_t n_rows);
  * and errors as fnlh_solve; rel_res (host, nullable) holds the rows' systems
  * one row after the other.  workspace as fnlh_relax_batched, with each row's
  * fnlh_workspace_bytes taken at `precision`.  When every row's prep blob has
- * FNLH_PREP_FF, no row has periodic edges and the workspace holds the sum of
+ * FNLH_PREP_FF and the workspace holds the sum of
  * the rows' fnlh_solve_workspace_bytes plus fnlh_batched_extra_bytes, the
  * intermediate checks of a mixed solve run in float-float as in fnlh_solve
  * (the check that ends the solve is FP64).  SYNCHRONISING. */
@@ -408,7 +409,7 @@ int fnlh_ilu_factor(const fnlh_mesh *mesh, const fnlh_jacobian *J, int32_t n_har
  * SYNCHRONISING.  Outputs (host, nullable): *iterations_done, rel_res [K].
  * Returns FNLH_ERR_NOT_CONVERGED after max_iterations, FNLH_ERR_NONFINITE /
  * FNLH_ERR_DIVERGED as fnlh_solve.  workspace: the FNLH_F64 size.  With an
- * FP32 factor and FNLH_PREP_FF in J's prep (no periodic edges), the residual
+ * FP32 factor and FNLH_PREP_FF in J's prep, the residual
  * of every iteration after the first is taken in float-float as in
  * fnlh_solve, and the one that ends the solve in FP64. */
 int fnlh_solve_ilu(const fnlh_mesh *mesh, const fnlh_jacobian *J, const fnlh_ilu *ilu, int32_t n_harm,

@@ -590,14 +590,14 @@ static int solve_ilu_typed(const fnlh_mesh* m, const fnlh_jacobian* J, const fnl
   const bool masking = (flags & FNLH_SOLVE_MASK_CONVERGED) != 0;
   bool x_zero = (flags & FNLH_SOLVE_ZERO_GUESS) != 0;
   if (x_zero) FNLH_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * sys.C * BS, s));
-  // Float-float checks (FP32 smoother, prep blob with FNLH_PREP_FF, no periodic
-  // edges), as in fnlh_solve: every residual after the first on the FP32 units
+  // Float-float checks (FP32 smoother, prep blob with FNLH_PREP_FF), as in
+  // fnlh_solve: every residual after the first on the FP32 units
   // from float-float shadows of B and x, a passing one confirmed at once in
   // FP64, and one that the decay predicts at or below 2 tol made in FP64
   // directly.  The shadows take the workspace's third vector and pivot-table
   // slots, which this solve does not use otherwise (each holds n C b float2).
   const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, J->block, J->prep_flags);
-  const bool ff = kRot && n > 0 && PL.offdff != (size_t)-1 && m->periodic == nullptr;
+  const bool ff = kRot && n > 0 && PL.offdff != (size_t)-1;
   float2* bff = ff ? at<float2>(ws, W.vec[2]) : nullptr;
   float2* xff = ff ? at<float2>(ws, W.pivinv) : nullptr;
   int it = 0, rc = FNLH_OK;

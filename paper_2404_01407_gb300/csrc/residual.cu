@@ -255,8 +255,35 @@ __global__ void __launch_bounds__(kResidualThreads) k_residual(const __grid_cons
 // registers and three CTAs); the rotation Q_i^T r to the sweeps' basis gathers the
 // node's rows with shuffles.  Writes Q_i^T r (FP32) like the FP64 kernel, and
 // per block the sums ||r_k||^2 and ||B_k||^2 (from B's high parts) in a
-// fixed order.  Not for meshes with periodic edges (no phase factors here).
+// fixed order.  Across a periodic edge (harmonics only) the row's product
+// y = J_ij x_j is formed on its own and enters the residual as e^{+-i sigma_k} y,
+// the phase factor split to float-float (ff_mul, ff_acc below).
 constexpr int kFfSys = 2;
+
+// a * b for float-float a and b, renormalised: the high parts' product
+// exactly (TwoProduct), the cross terms in FP32, then Fast2Sum.
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// (h, l) += v for a float-float v: TwoSum of the high parts, the low parts
+// added to l (the accumulator form of ff_sub_prod).
+__device__ __forceinline__ void ff_acc(float& h, float& l, float2 v) {
+  const float t = __fadd_rn(h, v.x);
+  const float z = __fsub_rn(t, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, z)), __fsub_rn(v.x, z));
+  h = t;
+  l = __fadd_rn(l, __fadd_rn(e, v.y));
+}
+
+// (h, l) as a renormalised float-float value (Fast2Sum: |l| small against h).
+__device__ __forceinline__ float2 ff_norm(float h, float l) {
+  const float t = __fadd_rn(h, l);
+  return make_float2(t, __fsub_rn(l, __fsub_rn(t, h)));
+}
 
 template <int BS>
 __global__ void __launch_bounds__(kResidualThreads, 4) k_residual_ff(const __grid_constant__ ResArgs a) {
@@ -297,7 +324,9 @@ __global__ void __launch_bounds__(kResidualThreads, 4) k_residual_ff(const __gri
       }
       // off-diagonal blocks: row q of J_ij times x_j for the pass's systems
       for (int p = p0; p < p1; ++p) {
-        const int j = col_of(a.col_idx[p]);
+        const int cj = a.col_idx[p];
+        const int j = col_of(cj);
+        const uint32_t side = side_of(cj);  // periodic edge: phase factor on the harmonics
         float2 jr[BS];
 #pragma unroll
         for (int t = 0; t < BS; ++t) jr[t] = a.offdff[((size_t)p * BS + q) * BS + t];
@@ -308,6 +337,25 @@ __global__ void __launch_bounds__(kResidualThreads, 4) k_residual_ff(const __gri
           if (k >= K) break;
           const int c0 = (k == 0) ? 0 : 2 * k - 1;
           const float2* xr = a.xff + ((size_t)j * C + c0) * BS;
+          if (side != 0 && k > 0) {
+            // y = -(J_ij x_j) of row q, then r += e^{+-i sigma_k} y
+            float yrh = 0.f, yrl = 0.f, yih = 0.f, yil = 0.f;
+#pragma unroll
+            for (int t = 0; t < BS; ++t) {
+              if (t == BS - 1 && skip_last) continue;
+              ff_sub_prod(yrh, yrl, jr[t], xr[t]);
+              ff_sub_prod(yih, yil, jr[t], xr[BS + t]);
+            }
+            const double2 ph = a.sys.phase[k];
+            const float2 c = ff_split(ph.x), sn = ff_split(side == kSideNext ? ph.y : -ph.y);
+            const float2 yr = ff_norm(yrh, yrl), yi = ff_norm(yih, yil);
+            const float2 sy = ff_mul(sn, yi), sx = ff_mul(sn, yr);
+            ff_acc(rh[s], rl[s], ff_mul(c, yr));
+            ff_acc(rh[s], rl[s], make_float2(-sy.x, -sy.y));
+            ff_acc(ih[s], il[s], sx);
+            ff_acc(ih[s], il[s], ff_mul(c, yi));
+            continue;
+          }
 #pragma unroll
           for (int t = 0; t < BS; ++t) {
             if (t == BS - 1 && skip_last) continue;

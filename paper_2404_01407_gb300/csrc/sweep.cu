@@ -745,7 +745,7 @@ int solve_typed(const fnlh_mesh* m, const fnlh_jacobian* J, int n_harm, const do
   // and a check that the residual's decay predicts at or below 2 tol is made
   // in FP64 directly, so that convergence is always certified in FP64.
   const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
-  const bool ff = mixed && n > 0 && PL.offdff != (size_t)-1 && m->periodic == nullptr && ws_bytes >= W.total_ff;
+  const bool ff = mixed && n > 0 && PL.offdff != (size_t)-1 && ws_bytes >= W.total_ff;
   float2* bff = ff ? at<float2>(ws, W.bff) : nullptr;
   float2* xff = ff ? at<float2>(ws, W.xff) : nullptr;
   if (ff) {
@@ -1163,15 +1163,14 @@ int solve_batched_typed(const fnlh_row* rows, int n_rows, int precision, double 
   BatchPlan P;
   const bool mixed = sizeof(T) == 4;
   // Float-float checks, as in fnlh_solve: every row's prep blob has the split
-  // blocks (FNLH_PREP_FF), no row has periodic edges, and the workspace holds
-  // every row's shadows of B and x.
+  // blocks (FNLH_PREP_FF) and the workspace holds every row's shadows of B and x.
   bool ff = mixed;
   {
     size_t need = batched_extra_bytes(n_rows);
     for (int r = 0; r < n_rows && ff; ++r) {
       const fnlh_jacobian* J = rows[r].J;
       const PrepLayout PL = prep_layout(J->n_nodes, J->nnz, BS, J->prep_flags);
-      if (PL.offdff == (size_t)-1 || rows[r].mesh->periodic != nullptr || J->n_nodes == 0) ff = false;
+      if (PL.offdff == (size_t)-1 || J->n_nodes == 0) ff = false;
       need += ws_layout(J->n_nodes, BS, rows[r].n_harm, precision).total_ff;
     }
     ff = ff && ws_bytes >= need;

@@ -207,3 +207,46 @@ def test_periodic_full_size_equals_ring():
     ref = _phase_shift(x, sigma, P)
     _gpu.assert_fp64_parity(RX.cpu().numpy(), ref, p.n_harm)
     torch.cuda.synchronize()
+
+
+FF_PREP = PREP | fnlh.FNLH_PREP_FF
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_periodic_float_float_checks_match_fp64(prec):
+    """The float-float residual applies e^{+-i sigma_l} to each periodic
+    entry's product: with two checks its norms are the FP64 residual's of the
+    same x (rounding apart); with three, the corrections it drives match the
+    FP64-checked solve's to rounding."""
+    p = inputs.problem((24, 16, 12), 6, 8, 20.0, 1.3, name="periodic_ff", periodic=True)
+    dm, J, B = _gpu.device_problem(p, prep_flags=FF_PREP)
+    n = p.mesh.n_nodes
+    ws_ff = fnlh.solve_workspace(n, 6, p.n_harm, FF_PREP, "cuda", prec)
+    ws_64 = fnlh.workspace(n, 6, p.n_harm, "cuda", prec)
+    zg = fnlh.FNLH_SOLVE_ZERO_GUESS
+    for checks in (2, 3):
+        X1, X2 = torch.zeros_like(B), torch.zeros_like(B)
+        st1, c1, s1, rel_ff = fnlh.fnlh_solve(dm, J, p.omega, B, X1, prec, 0.0, 12, checks, ws=ws_ff, flags=zg,
+                                              sigma=p.phase, raise_on_error=False)
+        st2, c2, s2, rel_64 = fnlh.fnlh_solve(dm, J, p.omega, B, X2, prec, 0.0, 12, checks, ws=ws_64, flags=zg,
+                                              sigma=p.phase, raise_on_error=False)
+        assert st1 == st2 == fnlh.FNLH_ERR_NOT_CONVERGED and c1 == c2 == checks
+        if checks == 2:  # the same x: the float-float norms are the FP64 ones up to rounding
+            assert torch.equal(X1, X2)
+            assert np.allclose(rel_ff, rel_64, rtol=1e-6, atol=0), (rel_ff, rel_64)
+        else:  # the second correction's FP32 right-hand side rounds a little differently
+            err = _gpu.rel_err_per_system(X1.cpu().numpy(), X2.cpu().numpy(), p.n_harm)
+            assert np.all(err <= 1e-8), err
+
+
+@pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
+def test_periodic_float_float_solve_certified_by_oracle(prec):
+    p = inputs.problem((24, 16, 12), 6, 8, 20.0, name="periodic_c3_reduced", periodic=True)
+    dm, J, B = _gpu.device_problem(p, prep_flags=FF_PREP)
+    X = torch.zeros_like(B)
+    st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 60,
+                                              flags=fnlh.FNLH_SOLVE_ZERO_GUESS, sigma=p.phase)
+    assert st == fnlh.FNLH_OK and np.all(rel <= 1e-8), (st, rel)
+    true_rel = oracle.rel_residuals(oracle_jac(p), p.mesh.vol, p.omega, p.b, X.cpu().numpy(), sigma=p.phase)
+    assert np.all(true_rel <= 1e-8), true_rel
+    assert np.allclose(rel, true_rel, rtol=1e-6, atol=1e-12), (rel, true_rel)
