@@ -90,7 +90,7 @@ enum fnlh_prep_flags {
     /* float-float copies (each FP64 entry as an FP32 pair hi + lo, |entry - hi - lo| <= 2^-48 |entry|) of
      * the off-diagonal blocks and of J_ii + D_i I in the original basis: with them, and the workspace of
      * fnlh_solve_workspace_bytes, the intermediate residual checks of a mixed-precision fnlh_solve run on
-     * the FP32 units (see fnlh_solve) */
+     * the FP32 units (see fnlh_solve; likewise fnlh_solve_batched and the FP32 fnlh_solve_ilu) */
     FNLH_PREP_FF = 16
 };
 

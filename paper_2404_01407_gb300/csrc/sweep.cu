@@ -10,7 +10,9 @@
 // accumulated in registers and the shifted diagonal system solved in
 // registers.  FP64: a CTA owns 32 nodes and each warp whole systems for them
 // (the mean flow's warp runs a real-only path).  FP32/BF16: 64-pair tiles
-// whose blocks are staged in shared memory when a node serves enough systems.
+// whose blocks are staged in shared memory when a node serves enough systems;
+// with one or two systems per node, one thread per node instead
+// (k_sweep_f32_node), each block loaded once for all of them.
 // The sweeps run in the per-node Hessenberg basis prepared by
 // fnlh_prepare (x = Q x~), where the diagonal block of system k is
 // H_i + i omega_k V_i I and its solve costs O(b^2).  Iterates live in the
