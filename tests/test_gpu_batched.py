@@ -31,12 +31,12 @@ def rows_problem():
             inputs.problem((10, 9, 7), 6, 4, 20.0, 2.3, seeds=(7, 8, 9))]
 
 
-def device_rows(probs, part=None):
+def device_rows(probs, part=None, prep=_gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS):
     dev = []
     for q, p in enumerate(probs):
         pa = None if part is None else part[q]
         dm = fnlh.DeviceMesh.from_mesh(p.mesh, "cuda", part=pa)
-        J = fnlh.DeviceJacobian(dm, p.block, _gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS)
+        J = fnlh.DeviceJacobian(dm, p.block, prep)
         fnlh.fnlh_build_jacobian(dm, torch.from_numpy(p.q).cuda(), fnlh.make_params(p.cfl), J)
         dev.append((p, dm, J, torch.from_numpy(p.b).cuda()))
     return dev
@@ -81,14 +81,18 @@ def test_batched_mixed_solve_reaches_1e8(prec):
         assert np.all(true_rel <= 1e-8), true_rel
 
 
-def test_batched_solve_with_partitioned_and_periodic_rows():
+@pytest.mark.parametrize("ff", [False, True])
+def test_batched_solve_with_partitioned_and_periodic_rows(ff):
+    """ff: float-float intermediate checks (with the periodic row's phase
+    factors and the partitioned row's full couplings)."""
     probs = [inputs.problem((12, 8, 6), 6, 4, 20.0, 1.6, seeds=(4, 5, 6)),
              inputs.problem((10, 6, 7), 6, 3, 20.0, 2.3, seeds=(7, 8, 9), periodic=True)]
     parts = [inputs.box_partition((12, 8, 6), (2, 2, 1)), None]
-    dev = device_rows(probs, parts)
+    prep = _gpu.ALL_PREP | fnlh.FNLH_PREP_TAGS | (fnlh.FNLH_PREP_FF if ff else 0)
+    dev = device_rows(probs, parts, prep=prep)
     Xs = [torch.zeros_like(B) for (_, _, _, B) in dev]
     batch = fnlh.BatchedRows([(dm, J, p.omega, B, X, p.phase) for (p, dm, J, B), X in zip(dev, Xs)])
-    ws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(batch.workspace_bytes(6, fnlh.FNLH_F32, ff=ff), dtype=torch.uint8, device="cuda")
     st, c, sw, rel = fnlh.fnlh_solve_batched(batch, fnlh.FNLH_F32, 1e-8, 12, 60, ws=ws)
     assert st == fnlh.FNLH_OK
     for X, p in zip(Xs, probs):
