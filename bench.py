@@ -53,8 +53,8 @@ BF16_INNER = 21  # BF16-block inner sweeps per correction (FP32 blocks: 30)
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
 # DRAM bytes (read + write) per launch of the top kernel from an ncu capture (profiles/k_sweep_f64_c2.md),
 # valid only while the kernel's sources hash to the value they had when it was taken
-NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363065344 + 177597696,
-                                  "sources_sha256": "b9b51d8dc2049f3eca1e03ca8f844eceaad11511cd4b81de555ca1b200f9d99b"}}
+NCU_TRAFFIC = {"k_sweep_f64_c2": {"bytes": 1363062784 + 177632768,
+                                  "sources_sha256": "144813b06f193bafef69f33c1fdd03e149971173103c471efb3cfa73f5c171bd"}}
 KERNEL_SOURCES = ("paper_2404_01407_gb300/csrc/sweep.cu", "paper_2404_01407_gb300/csrc/sweep_kernel.cuh",
                   "paper_2404_01407_gb300/csrc/common.cuh", "include/fnlh.h")
 
