@@ -303,12 +303,14 @@ def test_zero_sweeps_round_trips_the_basis():
 
 
 @pytest.mark.parametrize("prec", [fnlh.FNLH_F32, fnlh.FNLH_BF16])
-def test_mixed_solve_b5_and_permuted_numbering(prec):
-    """Euler blocks (b = 5) on a randomly renumbered mesh."""
+@pytest.mark.parametrize("ff", [False, True])
+def test_mixed_solve_b5_and_permuted_numbering(prec, ff):
+    """Euler blocks (b = 5) on a randomly renumbered mesh; ff: float-float
+    intermediate checks (the b = 5 form of the float-float residual)."""
     base = inputs.problem((14, 10, 8), 5, 3, 10.0, 1.3)
     mesh, perm = inputs.permute_mesh(base.mesh, seed=4)
     p = inputs.Problem(mesh=mesh, q=base.q[perm], b=base.b[perm], omega=base.omega, block=5, cfl=10.0)
-    dm, J, B = _gpu.device_problem(p)
+    dm, J, B = _gpu.device_problem(p, prep_flags=_gpu.ALL_PREP | (fnlh.FNLH_PREP_FF if ff else 0))
     X = torch.empty_like(B)
     st, checks, sweeps, rel = fnlh.fnlh_solve(dm, J, p.omega, B, X, prec, 1e-8, 12, 40,
                                               flags=fnlh.FNLH_SOLVE_ZERO_GUESS)
