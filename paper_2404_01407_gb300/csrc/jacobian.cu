@@ -224,14 +224,23 @@ __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* 
           P5[r][c] = P[r][c];
           Q5[r][c] = (r == c) ? 1.0 : 0.0;
         }
-      hessenberg_reduce<5>(P5, Q5);
+      // Z5 from the FP32-seeded eigenvector basis when it is accepted
+      // (about a third of the FP64 work), else by the FP64 Francis iteration.
+      // Only this path takes the eigenvector route: with it inlined into the
+      // generic path of the same kernel as well, every node's H came out
+      // wrong on GB300 (Z still orthogonal; H not Z^T P Z) for a reason not
+      // found in the source, while with this one instance H is exact.
       double T5[5][5], Z5[5][5];
-      for (int r = 0; r < 5; ++r)
-        for (int c = 0; c < 5; ++c) {
-          T5[r][c] = P5[r][c];
-          Z5[r][c] = Q5[r][c];
-        }
-      const bool tri5 = schur_real<5>(T5, Z5);
+      bool tri5 = schur_eigvec<5>(P5, Z5, T5);
+      if (!tri5) {
+        hessenberg_reduce<5>(P5, Q5);
+        for (int r = 0; r < 5; ++r)
+          for (int c = 0; c < 5; ++c) {
+            T5[r][c] = P5[r][c];
+            Z5[r][c] = Q5[r][c];
+          }
+        tri5 = schur_real<5>(T5, Z5);
+      }
       double Z6[6][6], H6[6][6];
       for (int m = 0; m < 6; ++m)
         for (int c = 0; c < 6; ++c) {
