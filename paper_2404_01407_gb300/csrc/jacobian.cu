@@ -228,8 +228,10 @@ __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* 
       // (about a third of the FP64 work), else by the FP64 Francis iteration.
       // Only this path takes the eigenvector route: with it inlined into the
       // generic path of the same kernel as well, every node's H came out
-      // wrong on GB300 (Z still orthogonal; H not Z^T P Z) for a reason not
-      // found in the source, while with this one instance H is exact.
+      // wrong on GB300 while Z stayed right -- read back, H held exactly what
+      // it would if T5 and H6 shared storage (H6's zero fill and its first
+      // entries showing through T5) -- although the source reads T5 only
+      // after writing it.  With this one instance H is exact.
       double T5[5][5], Z5[5][5];
       bool tri5 = schur_eigvec<5>(P5, Z5, T5);
       if (!tri5) {
