@@ -259,3 +259,89 @@ def test_float_float_prep_and_solve_workspace_sizes():
     w64 = fnlh.fnlh_workspace_bytes(n, b, N, fnlh.FNLH_F64)
     assert fnlh.fnlh_solve_workspace_bytes(n, b, N, fnlh.FNLH_F64, fnlh.FNLH_PREP_FF) == w64
     assert fnlh.fnlh_solve_workspace_bytes(n, 7, N, fnlh.FNLH_F32, fnlh.FNLH_PREP_FF) == 0
+
+
+def _fake_problem(prep_flags=fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32, part=None):
+    """A 4-node, edge-free mesh and Jacobian whose device pointers are fake
+    (aligned, never dereferenced): every call below must fail validation
+    before it launches or copies anything."""
+    a = ctypes.c_void_p(1 << 12)
+    m = fnlh.fnlh_mesh(4, 0, None, None, a, a, None, None, None, part)
+    nb = fnlh.fnlh_prep_bytes(4, 0, 6, prep_flags)
+    J = fnlh.fnlh_jacobian(4, 0, 6, None, a, a, ctypes.c_void_p(1 << 16), nb, prep_flags, 1)
+    return m, J, a
+
+
+def test_solve_validation_rejects_before_launch():
+    L = fnlh.lib()
+    m, J, a = _fake_problem()
+    om = (ctypes.c_double * 2)(1.0, 2.0)
+    c, s = ctypes.c_int32(), ctypes.c_int32()
+    rel = (ctypes.c_double * 3)()
+    ws_ok = fnlh.fnlh_workspace_bytes(4, 6, 2, fnlh.FNLH_F64)
+    ws = ctypes.c_void_p(1 << 20)
+
+    def solve(prec=fnlh.FNLH_F64, tol=1e-8, inner=10, checks=5, flags=0, w=ws, wb=ws_ok, n_harm=2, jac=J):
+        return L.fnlh_solve(ctypes.byref(m), ctypes.byref(jac), n_harm, om, None, a, a, prec, tol, inner, checks,
+                            flags, w, wb, ctypes.byref(c), ctypes.byref(s), rel, None)
+
+    assert solve(prec=9) == fnlh.FNLH_ERR_ARG
+    assert solve(tol=-1.0) == fnlh.FNLH_ERR_ARG
+    assert solve(tol=float("nan")) == fnlh.FNLH_ERR_ARG
+    assert solve(inner=0) == fnlh.FNLH_ERR_ARG
+    assert solve(checks=0) == fnlh.FNLH_ERR_ARG
+    assert solve(flags=1 << 7) == fnlh.FNLH_ERR_ARG
+    assert solve(n_harm=65) == fnlh.FNLH_ERR_UNSUPPORTED  # above the 64-harmonic maximum
+    assert solve(prec=fnlh.FNLH_BF16) == fnlh.FNLH_ERR_WORKSPACE  # prep holds no BF16 copy
+    assert solve(w=None) == fnlh.FNLH_ERR_WORKSPACE
+    assert solve(w=ctypes.c_void_p((1 << 20) + 8)) == fnlh.FNLH_ERR_ARG  # not 256-byte aligned
+    assert solve(wb=ws_ok - 1) == fnlh.FNLH_ERR_WORKSPACE
+    unready = fnlh.fnlh_jacobian(4, 0, 6, None, a, a, ctypes.c_void_p(1 << 16), J.prep_bytes, J.prep_flags, 0)
+    assert solve(jac=unready) == fnlh.FNLH_ERR_WORKSPACE
+
+
+def test_batched_validation_rejects_before_launch():
+    L = fnlh.lib()
+    m, J, a = _fake_problem()
+    om = (ctypes.c_double * 2)(1.0, 2.0)
+    rows = (fnlh.fnlh_row * 2)()
+    for r in rows:
+        r.mesh, r.J, r.n_harm, r.omega, r.B, r.X, r.sigma = ctypes.pointer(m), ctypes.pointer(J), 2, om, a, a, None
+    need = L.fnlh_batched_extra_bytes(2) + 2 * fnlh.fnlh_workspace_bytes(4, 6, 2, fnlh.FNLH_F32)
+    ws = ctypes.c_void_p(1 << 20)
+
+    def relax(rr=rows, n=2, sweeps=3, prec=fnlh.FNLH_F32, w=ws, wb=need):
+        return L.fnlh_relax_batched(rr, n, sweeps, prec, None, w, wb, None)
+
+    assert relax(rr=None) == fnlh.FNLH_ERR_ARG
+    assert relax(n=0) == fnlh.FNLH_ERR_ARG
+    assert relax(sweeps=-1) == fnlh.FNLH_ERR_ARG
+    assert relax(prec=9) == fnlh.FNLH_ERR_ARG
+    assert relax(prec=fnlh.FNLH_BF16) == fnlh.FNLH_ERR_WORKSPACE
+    assert relax(w=None) == fnlh.FNLH_ERR_WORKSPACE
+    assert relax(w=ctypes.c_void_p((1 << 20) + 16)) == fnlh.FNLH_ERR_ARG
+    assert relax(wb=need - 1) == fnlh.FNLH_ERR_WORKSPACE
+    # one bad row is enough: a block size the library has no kernels for
+    J7 = fnlh.fnlh_jacobian(4, 0, 7, None, a, a, ctypes.c_void_p(1 << 16), J.prep_bytes, J.prep_flags, 1)
+    rows[1].J = ctypes.pointer(J7)
+    assert relax() == fnlh.FNLH_ERR_UNSUPPORTED
+    rows[1].J = ctypes.pointer(J)
+
+    c, s = ctypes.c_int32(), ctypes.c_int32()
+    rel = (ctypes.c_double * 6)()
+
+    def solve(prec=fnlh.FNLH_F32, tol=1e-8, inner=10, checks=5, flags=0, wb=need):
+        return L.fnlh_solve_batched(rows, 2, prec, tol, inner, checks, flags, None, ws, wb, ctypes.byref(c),
+                                    ctypes.byref(s), rel, None)
+
+    assert solve(tol=float("nan")) == fnlh.FNLH_ERR_ARG
+    assert solve(inner=0) == fnlh.FNLH_ERR_ARG
+    assert solve(checks=0) == fnlh.FNLH_ERR_ARG
+    assert solve(flags=1 << 9) == fnlh.FNLH_ERR_ARG
+    assert solve(wb=need - 1) == fnlh.FNLH_ERR_WORKSPACE
+    # a partitioned row: plain FP64 Jacobi on truncated sweeps would not solve the full system
+    tags = fnlh.FNLH_PREP_F64 | fnlh.FNLH_PREP_F32 | fnlh.FNLH_PREP_TAGS
+    mp, Jp, _ = _fake_problem(tags, part=ctypes.c_void_p(1 << 14))
+    rows[0].mesh, rows[0].J = ctypes.pointer(mp), ctypes.pointer(Jp)
+    need64 = L.fnlh_batched_extra_bytes(2) + 2 * fnlh.fnlh_workspace_bytes(4, 6, 2, fnlh.FNLH_F64)
+    assert solve(prec=fnlh.FNLH_F64, wb=need64) == fnlh.FNLH_ERR_UNSUPPORTED
