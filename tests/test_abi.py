@@ -345,3 +345,39 @@ def test_batched_validation_rejects_before_launch():
     rows[0].mesh, rows[0].J = ctypes.pointer(mp), ctypes.pointer(Jp)
     need64 = L.fnlh_batched_extra_bytes(2) + 2 * fnlh.fnlh_workspace_bytes(4, 6, 2, fnlh.FNLH_F64)
     assert solve(prec=fnlh.FNLH_F64, wb=need64) == fnlh.FNLH_ERR_UNSUPPORTED
+
+
+def test_build_validation_rejects_before_launch():
+    """fnlh_build_jacobian's parameters (the pseudo-time reading of Eq. precon
+    needs CFL > 0, gamma > 1, a non-negative entropy-fix delta, and eps > 0 in
+    the block pseudo-time form) and the edge arrays the assembly reads."""
+    L = fnlh.lib()
+    a = ctypes.c_void_p(1 << 12)
+    m = fnlh.fnlh_mesh(4, 3, a, a, a, a, a, a, None)  # 3 edges: the assembly needs csr_edge, normals, edge_nodes
+    J = fnlh.fnlh_jacobian(4, 6, 6, a, a, a, None, 0, 0, 0)
+
+    def build(mesh=m, q=a, **kw):
+        p = fnlh.make_params(20.0)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return L.fnlh_build_jacobian(ctypes.byref(mesh), q, ctypes.byref(p), ctypes.byref(J), None)
+
+    assert build(cfl=0.0) == fnlh.FNLH_ERR_ARG
+    assert build(cfl=float("nan")) == fnlh.FNLH_ERR_ARG
+    assert build(gamma=1.0) == fnlh.FNLH_ERR_ARG
+    assert build(entropy_delta=-0.1) == fnlh.FNLH_ERR_ARG
+    assert build(pseudo_time=2) == fnlh.FNLH_ERR_ARG
+    assert build(pseudo_time=1, eps=0.0) == fnlh.FNLH_ERR_ARG
+    assert build(q=None) == fnlh.FNLH_ERR_ARG
+    assert L.fnlh_build_jacobian(ctypes.byref(m), a, None, ctypes.byref(J), None) == fnlh.FNLH_ERR_ARG
+    for field in ("csr_edge", "normals", "edge_nodes"):
+        bad = fnlh.fnlh_mesh(4, 3, a, a, a, a, a, a, None)
+        setattr(bad, field, None)
+        assert build(mesh=bad) == fnlh.FNLH_ERR_ARG, field
+    # nnz must be twice the edge count, the block size 5 or 6
+    J_bad = fnlh.fnlh_jacobian(4, 5, 6, a, a, a, None, 0, 0, 0)
+    assert L.fnlh_build_jacobian(ctypes.byref(m), a, ctypes.byref(fnlh.make_params(20.0)), ctypes.byref(J_bad),
+                                 None) == fnlh.FNLH_ERR_ARG
+    J_b4 = fnlh.fnlh_jacobian(4, 6, 4, a, a, a, None, 0, 0, 0)
+    assert L.fnlh_build_jacobian(ctypes.byref(m), a, ctypes.byref(fnlh.make_params(20.0)), ctypes.byref(J_b4),
+                                 None) == fnlh.FNLH_ERR_UNSUPPORTED
