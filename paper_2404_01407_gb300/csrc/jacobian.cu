@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(128) k_build_jacobian(BuildArgs a) {
 // under the block-diagonal change of basis x = Z x~, and in the new basis the
 // shifted diagonal solve of every system, (T_i + i omega V_i I) y = r, is a
 // back-substitution.  A block whose spectrum has a complex pair keeps the
-// Hessenberg form (the solve then eliminates first).
+// Hessenberg form (the solve then eliminates first).  The 5 x 5 mean-flow
+// block of a b = 6 frozen-turbulence node takes the cheaper FP32-seeded
+// eigenvector basis first (schur_eigvec), the FP64 iteration only where that
+// is not accepted.
 template <int BS>
 __global__ void __launch_bounds__(128) k_prepare_basis(int32_t n, const double* __restrict__ diag,
                                                        const double* __restrict__ D, double* __restrict__ rot,
